@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark: pair interactions/s of the full SPH-elastic right-hand side.
+
+Workload (default): one TOV neutron star of 1e5 equal-mass particles
+(M = 1.4 Msun, R = 12 km, Gamma = 2, outer 5 % of the radius solid crust with
+mu = 0.01 P, Y0 = 0.1, eps_break = 0.05, isotropic background metric, l = 0
+perturbation of 1e-3 c_s, h adapted to 60 +- 5 neighbours), mixed precision.
+A step is one kick-drift-kick step: Morton sort, neighbour lists, density,
+equation of state, pair forces, stress rate, background force, integration,
+yield scaling, damage test and h update.  Pairs = ordered neighbour pairs of
+the step's right-hand side.
+
+Multi-GPU (torchrun): every rank advances its own star (independent
+problems, weak scaling, no data-path collective); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s of full SPH-elastic RHS, FP32 vs FP64 at stated error"
+N_STAR = 100_000
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# Algorithmic FP32 flops per ordered pair (FMA = 2), counted from the formulas
+# as the kernels evaluate them once per pair: force pass 74 for a fluid pair
+# (+45 when either particle is solid), density pass 22.
+FLOPS_FORCE_PAIR = 74.0
+FLOPS_FORCE_SOLID_EXTRA = 45.0
+FLOPS_DENSITY_PAIR = 22.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_star(seed: int, n: int = N_STAR):
+    from paper_2107_07315_gb300 import inputs as I
+
+    st, eos, met, prof = I.star_state(n, seed=seed)
+    dt = I.cfl_dt(st, eos)
+    return st, eos, met, dt
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.out = os.path.join("/tmp", "sph_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.out):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_src: str):
+    """DRAM bytes per force-kernel launch from the committed ncu summary, or
+    None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "force_mixed_star1e5.md")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    src_ok, traffic = False, None
+    for line in open(path):
+        if line.startswith("kernel_source_sha256_16:") and line.split(":")[1].strip() == h:
+            src_ok = True
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                traffic = float(line.split(":")[1].strip())
+            except ValueError:
+                traffic = None
+    return traffic if src_ok else None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2107_07315_gb300 import inputs as I
+    from paper_2107_07315_gb300 import sph
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st, eos, met, dt = make_star(1 + rank, args.n)
+    n = len(st["x"])
+    prec = sph.SPH_MIXED if args.precision == "mixed" else sph.SPH_FP64
+    stream = torch.cuda.Stream()
+    dstate = sph.device_state(st, dev)
+    torch.cuda.synchronize()
+    ctx = sph.sph_init(dstate, eos, I.DEFAULT_MATERIAL, met, prec,
+                       dict(h_nmin=55, h_nmax=65, use_graph=1), stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sph.sph_timing(ctx, True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sph.sph_step(ctx, dt, 1)
+        sph.sph_sync(ctx)
+    sph.sph_timing_read(ctx)  # discard warm-up samples
+    stats0 = sph.sph_stats(ctx)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clk = ClockSampler(torch.cuda.current_device())
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict L2 between timed steps (outside the events)
+            evs[k][0].record(stream)
+            sph.sph_step(ctx, dt, 1)
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    sph.sph_sync(ctx)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ms = float(sum(step_ms))
+    tim = sph.sph_timing_read(ctx)
+    stats1 = sph.sph_stats(ctx)
+    pairs = float(stats1[1] - stats0[1])
+    # solid-pair share for the flop count (pairs touching a crust particle)
+    pairs_step = float(stats1[0])
+    solid_pairs = 0.0
+    if args.count_solid:
+        offs, idx = sph.neighbors(ctx)
+        ty = st["type"]
+        cnt = np.diff(offs)
+        owner = np.repeat(np.arange(n), cnt)
+        solid_pairs = float(np.count_nonzero((ty[owner] == 1) | (ty[idx] == 1)))
+    sph.sph_timing(ctx, False)
+
+    # end-to-end: host state in pinned memory -> device, step, device -> host
+    keys = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "S", "flags")
+    host = {k: dstate[k].cpu().pin_memory() for k in keys}
+    h2d = sum(host[k].numel() * host[k].element_size() for k in keys)
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    p_before = sph.sph_stats(ctx)[1]
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            for k in keys:
+                dstate[k].copy_(host[k], non_blocking=True)
+            sph.sph_step(ctx, dt, 1)
+            for k in keys:
+                host[k].copy_(dstate[k], non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_pairs = float(sph.sph_stats(ctx)[1] - p_before)
+    launches = int(stats1[3]) * args.steps
+
+    # aggregate over ranks: total pairs, max time
+    if ws > 1:
+        from paper_2107_07315_gb300 import shard
+
+        t_ms, pairs = shard.reduce_timing(t_ms, pairs, dev)
+        e2e_ms, e2e_pairs = shard.reduce_timing(e2e_ms, e2e_pairs, dev)
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+
+    value = pairs / (t_ms * 1e-3)
+    pk, src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    force_ms = tim[0] / max(tim[1], 1)
+    dens_ms = tim[2] / max(tim[3], 1)
+    build_ms = tim[6] / max(tim[7], 1)
+    flops_force = FLOPS_FORCE_PAIR * pairs_step + FLOPS_FORCE_SOLID_EXTRA * solid_pairs
+    achieved = flops_force / (force_ms * 1e-3) / 1e12
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2107_07315_gb300", "csrc",
+                                                "sph_pairs.cu"))
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "pairs/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == sph.SPH_MIXED else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "TOV star, %d particles (M=1.4, R=12 km, Gamma=2, 5%% crust), "
+                        "isotropic background, one KDK step per timed step incl. sort and "
+                        "neighbour lists" % n,
+            "precision": "mixed: FP32 pair sums (Kahan D, du), FP64 state/integration/totals"
+                         if prec == sph.SPH_MIXED else "fp64",
+            "n_particles": n,
+            "pairs_per_step": pairs_step,
+            "stars_per_gpu": 1,
+            "l2": "flushed between timed steps by a 256 MB write outside the events",
+            "parallelism": "independent star per GPU" if ws > 1 else "single GPU",
+        },
+        "roofline": {
+            "bound": "alu",
+            "kernel": "force pass (pair sums + finalize)",
+            "achieved": achieved,
+            "peak": peak_tflops,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops,
+            "traffic": traffic,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, src),
+            "kernel_ms": force_ms,
+            "density_kernel_ms": dens_ms,
+            "neighbour_build_ms": build_ms,
+            "flops_per_launch": flops_force,
+        },
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(st, eos, met, args.cpu_sample)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def oracle_sample_rhs(st, eos, met, sample: int, seed: int):
+    import oracle
+    from paper_2107_07315_gb300 import inputs as I
+
+    rng = np.random.default_rng(seed)
+    ids = np.sort(rng.choice(len(st["x"]), size=sample, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    r = oracle.rhs(st, eos, I.DEFAULT_MATERIAL, met, subset=ids)
+    t1 = time.perf_counter()
+    pairs = float(r["ncount"][ids].sum())
+    return pairs, t1 - t0
+
+
+def cpu_baseline(st, eos, met, sample: int):
+    import oracle
+
+    pairs, sec = oracle_sample_rhs(st, eos, met, sample, 7)
+    return {"value": pairs / sec, "unit": "pairs/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "right-hand side of %d random particles of the %d-particle star "
+                      "(brute-force O(N^2) neighbour search over all particles, FP64), "
+                      "%.1f s" % (sample, len(st["x"]), sec)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+
+    st, eos, met, _ = make_star(1, args.n)
+    for k in range(args.warmup):
+        oracle_sample_rhs(st, eos, met, max(args.cpu_sample // 8, 16), 100 + k)
+    tot_p, tot_s = 0.0, 0.0
+    for k in range(args.steps):
+        p, s = oracle_sample_rhs(st, eos, met, args.cpu_sample, 200 + k)
+        tot_p += p
+        tot_s += s
+    v = tot_p / tot_s
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "TOV star, %d particles, FP64 CPU oracle right-hand side on "
+                                  "a bounded particle sample per step" % len(st["x"]),
+                      "n_particles": len(st["x"])},
+           "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": oracle.num_threads(),
+                            "kind": "oracle",
+                            "sample": "%d random particles per step, brute-force neighbours"
+                                      % args.cpu_sample},
+           "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--n", type=int, default=N_STAR)
+    ap.add_argument("--cpu-sample", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count-solid", type=int, default=1)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * sph.h -- C ABI of libsph: the SPH right-hand side and time step for
+ * elastic-perfectly-plastic matter in a fixed GR background
+ * (arXiv 2107.07315, Sec. I.B "Solid SPH Equations", Sec. I.C "Fixed metric
+ * background", Sec. II.A equation of state).
+ *
+ * Conventions for every entry point:
+ *   - All particle and rate arrays are DEVICE memory owned by the caller,
+ *     structure-of-arrays, in the caller's particle order, length n unless
+ *     stated.  Symmetric tensors (S, dS, deps) are component-major:
+ *     component c of particle a at [c*n + a], order xx, yy, zz, xy, xz, yz;
+ *     the antisymmetric rotation rate dR holds xy, xz, yz the same way.
+ *   - EoS, material and metric descriptions are HOST memory; sph_init copies
+ *     them into memory the library owns.
+ *   - Particle buffers passed to sph_init are borrowed: they must stay valid
+ *     and in place until sph_free.  sph_step updates them in place.
+ *   - Work is enqueued on the CUDA stream given to sph_init.  Calls marked
+ *     "asynchronous" return after enqueueing; errors that only the device can
+ *     see (list capacity, non-finite state) are reported by sph_sync.
+ *   - Every call returns a status and never aborts.  There is no CPU path:
+ *     without a usable CUDA device the call returns SPH_ERR_NODEVICE.
+ *   - sph_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, ...) */
+    SPH_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    SPH_ERR_OOM = 3,        /* device allocation failed */
+    SPH_ERR_CAPACITY = 4,   /* a neighbour list exceeded its capacity */
+    SPH_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    SPH_ERR_NONFINITE = 6,  /* non-finite position, velocity or smoothing length */
+    SPH_ERR_BOUNDS = 7,     /* a checked index fell outside its buffer */
+    SPH_ERR_NODEVICE = 8    /* no usable CUDA device */
+} sph_status;
+
+typedef enum {
+    SPH_FP64 = 0,  /* pair sums and per-particle terms in FP64 (reference form) */
+    SPH_MIXED = 1  /* pair sums in FP32 (compensated density and energy sums),
+                      FP64 state, integration and totals */
+} sph_precision;
+
+/* Particle state (device, caller order).  Sec. I.B: positions x, velocity v
+ * (the coordinate velocity dx/dt of Sec. I.C when a metric is given),
+ * specific internal energy u, smoothing length h, baryonic mass m, deviatoric
+ * stress S.  type: 0 fluid core, 1 solid crust (Sec. III).  flags: bit0 set
+ * when the last step scaled S back to the yield surface, bit1 set (sticky)
+ * once the maximum-strain test fired.  star: star index per particle, or
+ * NULL for a single star; particles of different stars never interact.
+ * mu, Y0, eps_break: shear modulus, yield stress and breaking strain per
+ * particle (read for solid particles only; may be NULL if none is solid). */
+typedef struct {
+    int64_t n;
+    double *x, *y, *z, *vx, *vy, *vz, *u, *h, *m;
+    double *S;            /* 6*n */
+    uint8_t *type, *flags;
+    int32_t *star;        /* may be NULL */
+    double *mu, *Y0, *eps_break;
+} sph_particles;
+
+/* Polytropic equation of state per star, P = K rho^Gamma (Eq. poly_eos). */
+typedef struct {
+    int32_t nstars;
+    const double *K, *Gamma; /* host arrays of nstars */
+} sph_eos;
+
+/* Material and scheme options (host).  alpha_av, beta_av, eta2: Monaghan
+ * artificial viscosity Pi_ab (named in Sec. I.B, form not given there).
+ * jaumann: 0 objective rotation term R.S - S.R, 1 the printed S.R - R.S
+ * (Eq. solid4).  yield_mode: 0 f = min(Y0^2/sv^2, 1) as printed, 1 with the
+ * square root.  break_stress: 0 principal stresses of -P I + S, 1 of S.
+ * break_zero_S: 1 zeroes S and mu of a particle once it breaks. */
+typedef struct {
+    double alpha_av, beta_av, eta2;
+    int32_t jaumann, yield_mode, break_stress, break_zero_S;
+} sph_material;
+
+/* Fixed background metric (Sec. I.C), host tables.  kind 0: none.  kind 1:
+ * static isotropic ds^2 = -alpha^2 dt^2 + psi^4 dx.dx per star, tabulated
+ * on nr uniform nodes over [0, r_max[s]] around center[3*s..]: alpha,
+ * d alpha/dr, psi^4, d psi^4/dr (arrays of nstars*nr, star-major); beyond
+ * r_max the exterior Schwarzschild form with mass M[s].  pressure_form 0
+ * divides dP by W~^2 rho h (from div T = 0), 1 by W~ rho h as printed. */
+typedef struct {
+    int32_t kind, nstars, nr, pressure_form;
+    const double *r_max, *alpha, *dalpha, *psi4, *dpsi4, *M, *center;
+} sph_metric;
+
+/* Rates and derived fields (device, caller order), all length n unless
+ * noted: acceleration a (Eq. solid2 plus the background force of Sec. I.C),
+ * du/dt (Eq. solid3), continuity rate (Eq. solid1 with the computational
+ * density D of Sec. I.C), rest-mass density rho, pressure P, D, sound speed
+ * cs, strain rate deps (6n, Eq. solid5), rotation rate dR (3n, Eq. solid6),
+ * stress rate dS (6n, Eq. solid4), neighbour count ncount (int32). */
+typedef struct {
+    double *ax, *ay, *az, *dudt, *drhodt, *rho, *P, *D, *cs;
+    double *deps, *dR, *dS;
+    int32_t *ncount;
+} sph_rates;
+
+/* Run options (host); NULL in sph_init means the defaults in brackets.
+ * h_nmin, h_nmax: after each step multiply h by 1.0625 when the neighbour
+ * count is below h_nmin and by 0.9375 above h_nmax [0, 0: off].
+ * max_neighbors: per-particle neighbour list capacity [0: 128].
+ * lanes_per_particle: 4 or 8 threads share one particle's list in the pair
+ * kernels [0: automatic].  use_graph: capture each step in a CUDA graph [1].
+ * totals_every: compute totals every k steps inside sph_step [0: never]. */
+typedef struct {
+    int32_t h_nmin, h_nmax;
+    int32_t max_neighbors;
+    int32_t lanes_per_particle;
+    int32_t use_graph;
+    int32_t totals_every;
+} sph_options;
+
+/* Create a context bound to the particle buffers.  Validates the inputs,
+ * allocates scratch sized for n particles, copies EoS, material and metric
+ * to the device.  metric may be NULL (no background).  cuda_stream is a
+ * cudaStream_t (NULL: the legacy default stream).  Synchronous. */
+sph_status sph_init(sph_ctx **out, const sph_particles *particles, const sph_eos *eos,
+                    const sph_material *material, const sph_metric *metric,
+                    sph_precision precision, const sph_options *options, void *cuda_stream);
+
+/* Right-hand side at the bound state: Morton sort, neighbour lists, density
+ * summation (Sec. I.C "standard formula"), equation of state, pair sums of
+ * Eqs. solid1-solid6, stress rate (Eq. solid4) and background force
+ * (Sec. I.C), written to *out (device arrays of the caller).  Asynchronous. */
+sph_status sph_rhs(sph_ctx *ctx, const sph_rates *out);
+
+/* Advance nsteps kick-drift-kick steps of size dt: half kick, drift,
+ * right-hand side at the predicted velocity and stress, half kick, von Mises
+ * scaling (Sec. I.B), maximum-strain test (Sec. I.B), smoothing-length
+ * update.  Updates the bound particle buffers in place.  Asynchronous. */
+sph_status sph_step(sph_ctx *ctx, double dt, int32_t nsteps);
+
+/* Wait for the context's stream and report device-side errors raised since
+ * the last call (capacity, non-finite input, bounds, timeouts). */
+sph_status sph_sync(sph_ctx *ctx);
+
+/* Neighbour lists of the last right-hand side, CSR in caller order with
+ * ascending caller indices (b in N(a) iff b != a, same star and
+ * |x_a - x_b| < h_a + h_b, Sec. I.B).  offsets: device int64[n+1];
+ * idx: device int32[cap].  Returns SPH_ERR_CAPACITY (offsets written, idx
+ * not) when the lists hold more than cap entries.  Synchronous. */
+sph_status sph_neighbors(sph_ctx *ctx, int64_t *offsets, int32_t *idx, int64_t cap);
+
+/* Totals of the bound state, FP64, fixed reduction order (host out[16]):
+ * 0 mass, 1-3 momentum, 4 kinetic, 5 internal, 6 total energy, 7-9 angular
+ * momentum, 10 particles yielded in the last step, 11 broken particles,
+ * 12 mean neighbour count of the last right-hand side, 13-15 centre of
+ * mass.  Synchronous. */
+sph_status sph_totals(sph_ctx *ctx, double out[16]);
+
+/* Counters (host out[16]): 0 ordered neighbour pairs of the last right-hand
+ * side, 1 pairs summed over all right-hand sides, 2 right-hand sides
+ * evaluated, 3 kernel launches in one step, 4 tree leaves, 5 marginal pairs
+ * re-checked in FP64 (cumulative), 6 neighbour capacity per particle,
+ * 7 lanes per particle, 8 1 if steps run as a CUDA graph, 9 steps taken,
+ * 10 radix passes, 11 Morton bits per axis.  Synchronous. */
+sph_status sph_stats(sph_ctx *ctx, int64_t out[16]);
+
+/* Device-time measurement with CUDA events on the context's stream.
+ * enable 1 starts recording around the density and force kernels and
+ * whole steps; sph_timing_read returns (host out[8]): 0 summed ms of the
+ * force kernel, 1 its launches, 2 summed ms of the density kernel, 3 its
+ * launches, 4 summed ms of whole steps or right-hand sides, 5 their count,
+ * 6 summed ms of neighbour-list construction (sort through list build),
+ * 7 its launches.  Reading resets the sums.  Synchronous. */
+sph_status sph_timing(sph_ctx *ctx, int32_t enable);
+sph_status sph_timing_read(sph_ctx *ctx, double out[8]);
+
+/* Checkpoint: the bound particle state plus the rates carried between steps,
+ * flags and the step counter, as an opaque host blob.  sph_state_size gives
+ * its size; sph_get_state writes it; sph_set_state restores it so that
+ * continuing reproduces an uninterrupted run bit for bit.  Synchronous. */
+sph_status sph_state_size(sph_ctx *ctx, int64_t *bytes);
+sph_status sph_get_state(sph_ctx *ctx, void *host_buf, int64_t bytes);
+sph_status sph_set_state(sph_ctx *ctx, const void *host_buf, int64_t bytes);
+
+/* Release the context and its device memory (the caller's buffers stay). */
+void sph_free(sph_ctx *ctx);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *sph_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

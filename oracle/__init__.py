@@ -64,6 +64,10 @@ class _Metric(C.Structure):
                 ("dpsi4", _d), ("M", _d), ("center", _d)]
 
 
+class _Scales(C.Structure):
+    _fields_ = [(k, _d) for k in ("a", "du", "drho", "D", "eps", "dS")]
+
+
 class _Rates(C.Structure):
     _fields_ = [(k, _d) for k in ("ax", "ay", "az", "dudt", "drhodt", "rho", "P", "D", "cs",
                                   "deps", "dR", "dS")] + [("ncount", _i32)]
@@ -188,12 +192,14 @@ def num_threads() -> int:
 
 
 def rhs(state: dict, eos: dict, material: dict, metric=None, subset=None,
-        v=None, S=None) -> dict:
+        v=None, S=None, scales: bool = False) -> dict:
     """Rates of the full RHS (Eqs. solid1-solid6 + background force).
 
     ``subset``: optional int64 array of particle ids; only their rates are
     computed (other entries stay zero), using brute force over all particles.
     ``v`` (3 x n) and ``S`` (6 x n) override the state's velocity and stress.
+    ``scales``: also return r["scale"], the absolute-summand magnitudes
+    (keys a, du, drho, D, eps, dS) for cancellation-aware comparisons.
     """
     L = lib()
     s = _prep_state(state)
@@ -216,10 +222,17 @@ def rhs(state: dict, eos: dict, material: dict, metric=None, subset=None,
         sp, ns = _p(sub, _i64), len(sub)
     else:
         sub, sp, ns = None, None, 0
+    sc = None
+    if scales:
+        sc_arr = {k: np.zeros(n, np.float64) for k in ("a", "du", "drho", "D", "eps", "dS")}
+        sc = _Scales(*[_p(sc_arr[k]) for k in ("a", "du", "drho", "D", "eps", "dS")])
     rc = L.ora_rhs(C.byref(cs), _p(vx), _p(vy), _p(vz), _p(Sarr), C.byref(ce), C.byref(cm),
-                   C.byref(cg) if cg is not None else None, sp, C.c_int64(ns), C.byref(cr))
+                   C.byref(cg) if cg is not None else None, sp, C.c_int64(ns), C.byref(cr),
+                   C.byref(sc) if sc is not None else None)
     if rc != 0:
         raise MemoryError("oracle rhs failed")
+    if scales:
+        r["scale"] = sc_arr
     return r
 
 

@@ -76,6 +76,13 @@ typedef struct {
     int32_t *ncount;
 } ora_rates;
 
+/* Magnitude scales for cancellation-aware error measures: for each output,
+ * the same expression evaluated with every summand replaced by its absolute
+ * value (one value per particle; vectors and tensors share one scale). */
+typedef struct {
+    double *a, *du, *drho, *D, *eps, *dS;
+} ora_scales;
+
 /* ------------------------------------------------------------------------ */
 /* Smoothing kernel.  The paper uses W_ab = W(|r_a - r_b|, h_ab) with        */
 /* h_ab = (h_a + h_b)/2 (Sec. I.B, below Eq. solid4) and leaves the form     */
@@ -394,7 +401,8 @@ static double art_visc(const ora_material *mat, double hab, double vdx, double r
  */
 int ora_rhs(const ora_state *s, const double *vx, const double *vy, const double *vz,
             const double *S, const ora_eos *eos, const ora_material *mat,
-            const ora_metric *g, const int64_t *list, int64_t nlist, ora_rates *out)
+            const ora_metric *g, const int64_t *list, int64_t nlist, ora_rates *out,
+            ora_scales *scl)
 {
     int64_t n = s->n;
     int64_t cnt = list ? nlist : n;
@@ -450,6 +458,7 @@ int ora_rhs(const ora_state *s, const double *vx, const double *vy, const double
         double aP[3] = {0, 0, 0}, aV[3] = {0, 0, 0}, aS[3] = {0, 0, 0};
         double du = 0.0, dD = 0.0;
         double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}; /* sum m_b v_ba^i d_j W */
+        double sP = 0.0, sV = 0.0, sS = 0.0, sdu = 0.0, sdD = 0.0, sG = 0.0; /* magnitudes */
         double va[3] = {vx[a], vy[a], vz[a]};
         for (int64_t j = offs[k]; j < offs[k + 1]; ++j) {
             int64_t b = nb[j];
@@ -483,6 +492,18 @@ int ora_rhs(const ora_state *s, const double *vx, const double *vy, const double
             }
             du += mb * (pa->PD2 + 0.5 * Pi) * vgW;
             dD += (mb / pb->D) * vgW;
+            {
+                double gW = sqrt(gradW[0] * gradW[0] + gradW[1] * gradW[1] + gradW[2] * gradW[2]);
+                double dvn = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+                double Tn = 0.0;
+                for (int c = 0; c < 6; ++c) Tn += fabs(pa->SD2[c] + pb->SD2[c]) * (c < 3 ? 1.0 : 2.0);
+                sP += mb * (fabs(pa->PD2) + fabs(pb->PD2)) * gW;
+                sV += mb * fabs(Pi) * gW;
+                sS += mb * Tn * gW;
+                sdu += mb * (fabs(pa->PD2) + 0.5 * fabs(Pi)) * dvn * gW;
+                sdD += (mb / pb->D) * dvn * gW;
+                sG += mb * dvn * gW;
+            }
             if (solid_a)
                 for (int i = 0; i < 3; ++i)
                     for (int jj = 0; jj < 3; ++jj) G[i][jj] += mb * (-dv[i]) * gradW[jj];
@@ -512,12 +533,45 @@ int ora_rhs(const ora_state *s, const double *vx, const double *vy, const double
                     double J = mat->jaumann == 1 ? (SR - RS) : (RS - SR);
                     dS[i][jj] = 2.0 * mu * (eps[i][jj] - (i == jj ? tr / 3.0 : 0.0)) + J;
                 }
-            double Seps = 0.0;
+            double Seps = 0.0, Sn = 0.0;
             for (int i = 0; i < 3; ++i)
-                for (int jj = 0; jj < 3; ++jj) Seps += Sa[i][jj] * eps[i][jj];
+                for (int jj = 0; jj < 3; ++jj) {
+                    Seps += Sa[i][jj] * eps[i][jj];
+                    Sn += fabs(Sa[i][jj]);
+                }
             du += Seps / Da;
+            sdu += Sn * sG / (Da * Da);
         }
         double acc[3];
+        double sa = sP + sV + sS;
+        if (metric) {
+            double xd2 = va[0] * va[0] + va[1] * va[1] + va[2] * va[2];
+            double C0 = g->pressure_form == 1 ? 1.0 / (pa->Wt * pa->rho * pa->henth)
+                                              : 1.0 / (pa->Wt * pa->Wt * pa->rho * pa->henth);
+            double ga = sqrt(pa->grad_alpha[0] * pa->grad_alpha[0] + pa->grad_alpha[1] * pa->grad_alpha[1] +
+                             pa->grad_alpha[2] * pa->grad_alpha[2]);
+            double gq = sqrt(pa->grad_psi4[0] * pa->grad_psi4[0] + pa->grad_psi4[1] * pa->grad_psi4[1] +
+                             pa->grad_psi4[2] * pa->grad_psi4[2]);
+            double xn = sqrt(xd2);
+            double sGam = xd2 * gq + pa->alpha * ga + 0.5 * gq * xd2;
+            double sdt = pa->cP * (pa->rho / Da) * Da * sdD + xn * Da * sP;
+            sa = (C0 * Da * sP + sGam) / pa->psi4 +
+                 xn / (pa->alpha * pa->alpha) * (C0 * sdt + 2.0 * pa->alpha * xn * ga) + sV + sS;
+        }
+        if (scl) {
+            scl->a[a] = sa;
+            scl->du[a] = sdu;
+            scl->drho[a] = Da * sdD;
+            scl->D[a] = Da;
+            scl->eps[a] = sG / Da;
+            if (solid_a) {
+                double Sn = 0.0;
+                for (int c = 0; c < 6; ++c) Sn += fabs(S[(int64_t)c * n + a]) * (c < 3 ? 1.0 : 2.0);
+                scl->dS[a] = 2.0 * fabs(s->mu[a]) * sG / Da + 2.0 * Sn * sG / Da;
+            } else {
+                scl->dS[a] = 0.0;
+            }
+        }
         if (metric) {
             double xdot[3] = {va[0], va[1], va[2]};
             double C = g->pressure_form == 1 ? 1.0 / (pa->Wt * pa->rho * pa->henth)
@@ -678,7 +732,7 @@ int ora_step(ora_state *s, const ora_eos *eos, const ora_material *mat, const or
 {
     int64_t n = s->n;
     if (!have_rates) {
-        if (ora_rhs(s, s->vx, s->vy, s->vz, s->S, eos, mat, g, NULL, 0, r)) return 1;
+        if (ora_rhs(s, s->vx, s->vy, s->vz, s->S, eos, mat, g, NULL, 0, r, NULL)) return 1;
     }
     double *vp = (double *)malloc(sizeof(double) * (size_t)(3 * n + 1));
     double *Sp = (double *)malloc(sizeof(double) * (size_t)(6 * n + 1));
@@ -702,7 +756,7 @@ int ora_step(ora_state *s, const ora_eos *eos, const ora_material *mat, const or
                 Sp[i] = s->S[i] + hdt * r->dS[i];
             }
         }
-        if (ora_rhs(s, vp, vp + n, vp + 2 * n, Sp, eos, mat, g, NULL, 0, r)) {
+        if (ora_rhs(s, vp, vp + n, vp + 2 * n, Sp, eos, mat, g, NULL, 0, r, NULL)) {
             free(vp); free(Sp); return 1;
         }
         for (int64_t a = 0; a < n; ++a) {

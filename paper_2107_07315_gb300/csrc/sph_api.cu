@@ -1,0 +1,810 @@
+// C ABI of libsph (declared in include/sph.h): context set-up, the
+// right-hand side and step sequences, CUDA-graph capture of steps,
+// event timing, totals, neighbour export and checkpoints.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+sph_status fail(sph_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA,     \
+                        "%s: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+
+struct TimingSlot {
+    cudaEvent_t ev[6];  // step start, build start, density start, force start, force end, step end
+};
+
+}  // namespace
+
+struct sph_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    int nstars = 1;
+    sph_precision prec = SPH_MIXED;
+    sph_options opt{};
+    sph_particles P{};
+    bool any_solid = false;
+    // owned device memory
+    std::vector<void *> allocs;
+    double *d_K = nullptr, *d_Gamma = nullptr;
+    DevMaterial mat{};
+    DevMetric met{};
+    Scratch s{};
+    SortPlan plan{};
+    TreeLevels tl{};
+    int nleaves = 0;
+    int cap = 128;
+    int lanes = 8;
+    DevRates r{};
+    double *vp = nullptr, *Sp = nullptr;
+    double *tot_partial = nullptr, *tot_out = nullptr;
+    double *zeros = nullptr;  // stand-in for absent per-particle material arrays
+    int have_rates = 0;
+    int64_t steps = 0;
+    int launches_per_step = 0;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    double gdt = 0.0;
+    int gtiming = 0;
+    cudaGraphNode_t gev_nodes[6] = {};
+    // timing
+    int timing = 0;
+    std::vector<TimingSlot> slots;
+    int slot_used = 0;
+    int slot_kind_step = 0;
+
+    template <typename T>
+    sph_status alloc(T **p, size_t count)
+    {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return fail(SPH_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                        cudaGetErrorString(e));
+        }
+        allocs.push_back((void *)*p);
+        return SPH_OK;
+    }
+};
+
+namespace {
+
+#define STATUS_TRY(call)                 \
+    do {                                 \
+        sph_status s_ = (call);          \
+        if (s_ != SPH_OK) return s_;     \
+    } while (0)
+
+DevState state_of(const sph_ctx *c, const double *vx, const double *vy, const double *vz,
+                  const double *S)
+{
+    DevState st;
+    st.n = c->n;
+    st.x = c->P.x;
+    st.y = c->P.y;
+    st.z = c->P.z;
+    st.vx = vx;
+    st.vy = vy;
+    st.vz = vz;
+    st.S = S;
+    st.h = c->P.h;
+    st.m = c->P.m;
+    st.mu = c->P.mu ? c->P.mu : c->zeros;
+    st.type = c->P.type;
+    st.star = c->P.star;
+    return st;
+}
+
+StepState step_state_of(sph_ctx *c)
+{
+    StepState s;
+    s.n = c->n;
+    s.x = c->P.x;
+    s.y = c->P.y;
+    s.z = c->P.z;
+    s.vx = c->P.vx;
+    s.vy = c->P.vy;
+    s.vz = c->P.vz;
+    s.u = c->P.u;
+    s.h = c->P.h;
+    s.S = c->P.S;
+    s.m = c->P.m;
+    s.type = c->P.type;
+    s.flags = c->P.flags;
+    s.star = c->P.star;
+    s.mu = c->P.mu ? c->P.mu : c->zeros;
+    s.Y0 = c->P.Y0 ? c->P.Y0 : c->zeros;
+    s.eps_break = c->P.eps_break ? c->P.eps_break : c->zeros;
+    s.vp = c->vp;
+    s.Sp = c->Sp;
+    return s;
+}
+
+DevEos eos_of(const sph_ctx *c)
+{
+    DevEos e;
+    e.K = c->d_K;
+    e.Gamma = c->d_Gamma;
+    return e;
+}
+
+DevRates rates_of(const sph_rates *o)
+{
+    DevRates r;
+    r.ax = o->ax;
+    r.ay = o->ay;
+    r.az = o->az;
+    r.dudt = o->dudt;
+    r.drhodt = o->drhodt;
+    r.rho = o->rho;
+    r.P = o->P;
+    r.D = o->D;
+    r.cs = o->cs;
+    r.deps = o->deps;
+    r.dR = o->dR;
+    r.dS = o->dS;
+    r.ncount = o->ncount;
+    return r;
+}
+
+sph_status ensure_slot(sph_ctx *c)
+{
+    if (c->slot_used < (int)c->slots.size()) return SPH_OK;
+    size_t old = c->slots.size();
+    c->slots.resize(old + 256);
+    for (size_t k = old; k < c->slots.size(); ++k)
+        for (int e = 0; e < 6; ++e) CUDA_TRY(cudaEventCreate(&c->slots[k].ev[e]));
+    return SPH_OK;
+}
+
+// Events of the current timing slot (or null when timing is off).
+cudaEvent_t slot_ev(sph_ctx *c, int e)
+{
+    if (!c->timing) return nullptr;
+    return c->slots[c->slot_used].ev[e];
+}
+
+void rec(sph_ctx *c, cudaEvent_t ev, bool capturing)
+{
+    if (!ev) return;
+    if (capturing) cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ev, c->stream);
+}
+
+// The right-hand side on the given velocity and stress, into `out`.
+void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool capturing,
+                 int *nlaunch)
+{
+    if (c->n == 0) return;
+    rec(c, slot_ev(c, 1), capturing);
+    launch_build(st, c->s, c->plan, c->tl, c->nleaves, c->cap, c->prec == SPH_FP64, c->stream,
+                 nlaunch);
+    rec(c, slot_ev(c, 2), capturing);
+    launch_density(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
+                   c->stream);
+    rec(c, slot_ev(c, 3), capturing);
+    launch_force(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
+                 c->stream);
+    rec(c, slot_ev(c, 4), capturing);
+    if (nlaunch) *nlaunch += 2;
+}
+
+void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch)
+{
+    StepState ss = step_state_of(c);
+    rec(c, slot_ev(c, 0), capturing);
+    launch_kick_drift(ss, c->r, dt, c->stream);
+    DevState st = state_of(c, c->vp, c->vp + c->n, c->vp + 2 * c->n, c->Sp);
+    enqueue_rhs(c, st, c->r, capturing, nlaunch);
+    launch_kick_return(ss, c->r, eos_of(c), c->mat, dt, c->opt.h_nmin, c->opt.h_nmax, c->stream);
+    rec(c, slot_ev(c, 5), capturing);
+    if (nlaunch) *nlaunch += 2;
+}
+
+void drop_graph(sph_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+}
+
+sph_status capture_step(sph_ctx *c, double dt)
+{
+    drop_graph(c);
+    cudaGraph_t graph = nullptr;
+    // Timing slot 0's events mark the nodes; replays swap in the slot's events.
+    int saved_used = c->slot_used;
+    if (c->timing) {
+        STATUS_TRY(ensure_slot(c));
+    }
+    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int nl = 0;
+    enqueue_step(c, dt, true, &nl);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (e != cudaSuccess) return fail(SPH_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        c->gexec = nullptr;
+        return fail(SPH_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    for (int k = 0; k < 6; ++k) c->gev_nodes[k] = nullptr;
+    if (c->timing) {
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(graph, nodes.data(), &nn);
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            cudaGraphNodeGetType(nd, &ty);
+            if (ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            cudaGraphEventRecordNodeGetEvent(nd, &ev);
+            for (int k = 0; k < 6; ++k)
+                if (ev == c->slots[saved_used].ev[k]) c->gev_nodes[k] = nd;
+        }
+    }
+    cudaGraphDestroy(graph);
+    c->gdt = dt;
+    c->gtiming = c->timing;
+    c->launches_per_step = nl;
+    return SPH_OK;
+}
+
+int bits_for(int64_t n)
+{
+    int lg = 1;
+    while ((1ll << lg) < n) ++lg;
+    int b = (lg + 2) / 3 + 2;
+    return b < 5 ? 5 : (b > 10 ? 10 : b);
+}
+
+sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_material *mat,
+                    const sph_metric *g, sph_precision prec, const sph_options *opt)
+{
+    if (!p) return fail(SPH_ERR_ARG, "particles is NULL");
+    if (p->n < 0 || p->n > 0x7fffff00ll) return fail(SPH_ERR_ARG, "n = %lld out of range", (long long)p->n);
+    if (p->n > 0) {
+        if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->u || !p->h || !p->m ||
+            !p->S || !p->type || !p->flags)
+            return fail(SPH_ERR_ARG, "a required particle array is NULL");
+    }
+    if (!eos || eos->nstars < 1 || eos->nstars > 65535 || !eos->K || !eos->Gamma)
+        return fail(SPH_ERR_ARG, "eos must give 1..65535 stars with K and Gamma");
+    for (int s = 0; s < eos->nstars; ++s) {
+        if (!(eos->Gamma[s] > 1.0) || !(eos->K[s] > 0.0) || !std::isfinite(eos->Gamma[s]) ||
+            !std::isfinite(eos->K[s]))
+            return fail(SPH_ERR_ARG, "star %d: need K > 0 and Gamma > 1", s);
+    }
+    if (!mat) return fail(SPH_ERR_ARG, "material is NULL");
+    if (mat->jaumann < 0 || mat->jaumann > 1 || mat->yield_mode < 0 || mat->yield_mode > 1 ||
+        mat->break_stress < 0 || mat->break_stress > 1)
+        return fail(SPH_ERR_ARG, "material option out of range");
+    if (prec != SPH_FP64 && prec != SPH_MIXED) return fail(SPH_ERR_ARG, "unknown precision");
+    if (g && g->kind != 0) {
+        if (g->kind != 1) return fail(SPH_ERR_ARG, "metric kind must be 0 or 1");
+        if (g->nstars != eos->nstars) return fail(SPH_ERR_ARG, "metric and eos star counts differ");
+        if (g->nr < 2) return fail(SPH_ERR_ARG, "metric needs nr >= 2");
+        if (!g->r_max || !g->alpha || !g->dalpha || !g->psi4 || !g->dpsi4 || !g->M || !g->center)
+            return fail(SPH_ERR_ARG, "a metric table is NULL");
+        if (g->pressure_form < 0 || g->pressure_form > 1)
+            return fail(SPH_ERR_ARG, "metric pressure_form must be 0 or 1");
+        for (int s = 0; s < g->nstars; ++s)
+            if (!(g->r_max[s] > 0.0)) return fail(SPH_ERR_ARG, "metric r_max must be > 0");
+    }
+    if (opt) {
+        if (opt->max_neighbors < 0 || opt->max_neighbors > 4096)
+            return fail(SPH_ERR_ARG, "max_neighbors out of range");
+        if (opt->lanes_per_particle != 0 && opt->lanes_per_particle != 4 &&
+            opt->lanes_per_particle != 8)
+            return fail(SPH_ERR_ARG, "lanes_per_particle must be 0, 4 or 8");
+        if (opt->h_nmax < 0 || opt->h_nmin < 0 || (opt->h_nmax > 0 && opt->h_nmin > opt->h_nmax))
+            return fail(SPH_ERR_ARG, "h_nmin/h_nmax band invalid");
+    }
+    return SPH_OK;
+}
+
+sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
+                     const sph_material *mat, const sph_metric *g, sph_precision prec,
+                     const sph_options *opt, void *stream)
+{
+    c->P = *p;
+    c->n = p->n;
+    c->nstars = eos->nstars;
+    c->prec = prec;
+    if (opt) c->opt = *opt;
+    else {
+        c->opt = sph_options{};
+        c->opt.use_graph = 1;
+    }
+    c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : 128;
+    c->lanes = c->opt.lanes_per_particle > 0 ? c->opt.lanes_per_particle : 8;
+    c->stream = (cudaStream_t)stream;
+    CUDA_TRY(cudaGetDevice(&c->device));
+    const int64_t n = c->n;
+    // Host copies of type and star: star layout, solid check.
+    std::vector<int32_t> star(n > 0 ? n : 1, 0);
+    std::vector<uint8_t> type(n > 0 ? n : 1, 0);
+    if (n > 0) {
+        if (p->star) CUDA_TRY(cudaMemcpy(star.data(), p->star, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(type.data(), p->type, n * sizeof(uint8_t), cudaMemcpyDeviceToHost));
+    }
+    std::vector<int64_t> per(c->nstars, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (star[i] < 0 || star[i] >= c->nstars)
+            return fail(SPH_ERR_ARG, "particle %lld has star %d outside [0, %d)", (long long)i,
+                        star[i], c->nstars);
+        if (type[i] > 1) return fail(SPH_ERR_ARG, "particle %lld has type %d", (long long)i, type[i]);
+        per[star[i]]++;
+        c->any_solid |= type[i] == 1;
+    }
+    if (c->any_solid && (!p->mu || !p->Y0 || !p->eps_break))
+        return fail(SPH_ERR_ARG, "solid particles need mu, Y0 and eps_break arrays");
+    // Leaves: 8 consecutive sorted particles of one star (stars are sorted by id).
+    std::vector<int32_t> leaf_start(1, 0), leaf_star, leaf_of(n > 0 ? n : 1, 0);
+    int64_t pos = 0;
+    for (int s = 0; s < c->nstars; ++s) {
+        for (int64_t k = 0; k < per[s]; k += kLeaf) {
+            int64_t e = pos + (per[s] - k < kLeaf ? per[s] - k : kLeaf);
+            for (int64_t i = pos; i < e; ++i) leaf_of[i] = (int32_t)leaf_star.size();
+            leaf_star.push_back(s);
+            leaf_start.push_back((int32_t)e);
+            pos = e;
+        }
+    }
+    c->nleaves = (int)leaf_star.size();
+    // Tree levels.
+    c->tl.nlevels = 0;
+    int64_t total_nodes = 0;
+    if (c->nleaves > 0) {
+        int cnt = c->nleaves;
+        while (true) {
+            if (c->tl.nlevels >= kMaxLevels) return fail(SPH_ERR_ARG, "too many tree levels");
+            c->tl.count[c->tl.nlevels] = cnt;
+            c->tl.offset[c->tl.nlevels] = (int)total_nodes;
+            total_nodes += cnt;
+            c->tl.nlevels++;
+            if (cnt == 1) break;
+            cnt = (cnt + 1) / 2;
+        }
+    }
+    // Sort plan.
+    int sb = 0;
+    while ((1 << sb) < c->nstars) ++sb;
+    c->plan.key_bits_axis = bits_for(n);
+    c->plan.star_bits = sb;
+    int kb = 3 * c->plan.key_bits_axis + sb;
+    c->plan.passes = (kb + 7) / 8;
+    int64_t per_tile = 256ll * 304;
+    int ipt = (int)((n + per_tile - 1) / per_tile);
+    c->plan.ipt = ipt < 1 ? 1 : (ipt > 16 ? 16 : ipt);
+    c->plan.nblocks = (int)((n + 256ll * c->plan.ipt - 1) / (256ll * c->plan.ipt));
+    if (c->plan.nblocks < 1) c->plan.nblocks = 1;
+    // Device memory.
+    const int64_t nn = n > 0 ? n : 1;
+    Scratch &s = c->s;
+    STATUS_TRY(c->alloc(&s.perm, nn));
+    STATUS_TRY(c->alloc(&s.keys[0], nn));
+    STATUS_TRY(c->alloc(&s.keys[1], nn));
+    STATUS_TRY(c->alloc(&s.vals[0], nn));
+    STATUS_TRY(c->alloc(&s.vals[1], nn));
+    STATUS_TRY(c->alloc(&s.hist, (size_t)c->plan.passes * 256 * c->plan.nblocks));
+    STATUS_TRY(c->alloc(&s.xs, nn));
+    STATUS_TRY(c->alloc(&s.ys, nn));
+    STATUS_TRY(c->alloc(&s.zs, nn));
+    STATUS_TRY(c->alloc(&s.hs, nn));
+    STATUS_TRY(c->alloc(&s.tys, nn));
+    STATUS_TRY(c->alloc(&s.rec, 4 * nn));
+    STATUS_TRY(c->alloc(&s.sd2, 2 * nn));
+    STATUS_TRY(c->alloc(&s.pp, 2 * nn));
+    if (prec == SPH_FP64) {
+        STATUS_TRY(c->alloc(&s.rec64, 3 * nn));
+        STATUS_TRY(c->alloc(&s.sd264, 8 * nn));
+        STATUS_TRY(c->alloc(&s.pp64, 8 * nn));
+    }
+    STATUS_TRY(c->alloc(&s.nbr, (size_t)nn * c->cap));
+    STATUS_TRY(c->alloc(&s.ncnt, nn));
+    STATUS_TRY(c->alloc(&s.nodes, 2 * (size_t)(total_nodes > 0 ? total_nodes : 1)));
+    STATUS_TRY(c->alloc(&s.leaf_start, leaf_start.size()));
+    STATUS_TRY(c->alloc(&s.leaf_star, leaf_star.size() > 0 ? leaf_star.size() : 1));
+    STATUS_TRY(c->alloc(&s.leaf_of, nn));
+    STATUS_TRY(c->alloc(&s.bbox_partial, 6 * kBoxBlocksMax));
+    STATUS_TRY(c->alloc(&s.bbox_done, 1));
+    STATUS_TRY(c->alloc(&s.sc, 1));
+    CUDA_TRY(cudaMemset(s.bbox_done, 0, sizeof(unsigned int)));
+    CUDA_TRY(cudaMemset(s.sc, 0, sizeof(DevScalars)));
+    CUDA_TRY(cudaMemcpy(s.leaf_start, leaf_start.data(), leaf_start.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+    if (!leaf_star.empty())
+        CUDA_TRY(cudaMemcpy(s.leaf_star, leaf_star.data(), leaf_star.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(s.leaf_of, leaf_of.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // Rates carried between steps, predicted velocity and stress, totals.
+    DevRates &r = c->r;
+    for (double **f : {&r.ax, &r.ay, &r.az, &r.dudt, &r.drhodt, &r.rho, &r.P, &r.D, &r.cs})
+        STATUS_TRY(c->alloc(f, nn));
+    STATUS_TRY(c->alloc(&r.deps, 6 * nn));
+    STATUS_TRY(c->alloc(&r.dR, 3 * nn));
+    STATUS_TRY(c->alloc(&r.dS, 6 * nn));
+    STATUS_TRY(c->alloc(&r.ncount, nn));
+    CUDA_TRY(cudaMemset(r.ncount, 0, nn * sizeof(int32_t)));
+    STATUS_TRY(c->alloc(&c->vp, 3 * nn));
+    STATUS_TRY(c->alloc(&c->Sp, 6 * nn));
+    STATUS_TRY(c->alloc(&c->tot_partial, 16 * kTotalsBlocks));
+    STATUS_TRY(c->alloc(&c->tot_out, 16));
+    STATUS_TRY(c->alloc(&c->zeros, nn));
+    CUDA_TRY(cudaMemset(c->zeros, 0, nn * sizeof(double)));
+    // EoS, material, metric.
+    STATUS_TRY(c->alloc(&c->d_K, c->nstars));
+    STATUS_TRY(c->alloc(&c->d_Gamma, c->nstars));
+    CUDA_TRY(cudaMemcpy(c->d_K, eos->K, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_Gamma, eos->Gamma, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
+    c->mat.alpha_av = mat->alpha_av;
+    c->mat.beta_av = mat->beta_av;
+    c->mat.eta2 = mat->eta2;
+    c->mat.jaumann = mat->jaumann;
+    c->mat.yield_mode = mat->yield_mode;
+    c->mat.break_stress = mat->break_stress;
+    c->mat.break_zero_S = mat->break_zero_S;
+    c->met = DevMetric{};
+    c->met.kind = 0;
+    if (g && g->kind == 1) {
+        int ns = g->nstars, nr = g->nr;
+        c->met.kind = 1;
+        c->met.nstars = ns;
+        c->met.nr = nr;
+        c->met.pressure_form = g->pressure_form;
+        std::vector<double> tab((size_t)ns * nr * 4);
+        std::vector<float> tabf(tab.size());
+        for (size_t k = 0; k < (size_t)ns * nr; ++k) {
+            tab[4 * k + 0] = g->alpha[k];
+            tab[4 * k + 1] = g->dalpha[k];
+            tab[4 * k + 2] = g->psi4[k];
+            tab[4 * k + 3] = g->dpsi4[k];
+        }
+        for (size_t k = 0; k < tab.size(); ++k) tabf[k] = (float)tab[k];
+        double *d_tab, *d_rmax, *d_M, *d_center;
+        float *d_tabf;
+        STATUS_TRY(c->alloc(&d_tab, tab.size()));
+        STATUS_TRY(c->alloc(&d_tabf, tabf.size()));
+        STATUS_TRY(c->alloc(&d_rmax, ns));
+        STATUS_TRY(c->alloc(&d_M, ns));
+        STATUS_TRY(c->alloc(&d_center, 3 * ns));
+        CUDA_TRY(cudaMemcpy(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(d_tabf, tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(d_rmax, g->r_max, ns * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(d_M, g->M, ns * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(d_center, g->center, 3 * ns * sizeof(double), cudaMemcpyHostToDevice));
+        c->met.tab = d_tab;
+        c->met.tabf = d_tabf;
+        c->met.r_max = d_rmax;
+        c->met.M = d_M;
+        c->met.center = d_center;
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    return SPH_OK;
+}
+
+int64_t state_blob_size(const sph_ctx *c)
+{
+    // header (8 int64) + doubles: x y z vx vy vz u h mu Y0 eps (11n) + S (6n)
+    // + rates ax ay az dudt (4n) + dS (6n) + type, flags (2n bytes)
+    return 64 + 8 * (27 * c->n) + 2 * c->n;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_init(sph_ctx **out, const sph_particles *particles, const sph_eos *eos,
+                    const sph_material *material, const sph_metric *metric,
+                    sph_precision precision, const sph_options *options, void *cuda_stream)
+{
+    g_err[0] = 0;
+    if (!out) return fail(SPH_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    sph_status st = validate(particles, eos, material, metric, precision, options);
+    if (st != SPH_OK) return st;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(SPH_ERR_NODEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    sph_ctx *c = new (std::nothrow) sph_ctx();
+    if (!c) return fail(SPH_ERR_OOM, "host allocation failed");
+    st = init_impl(c, particles, eos, material, metric, precision, options, cuda_stream);
+    if (st != SPH_OK) {
+        char keep[512];
+        memcpy(keep, g_err, sizeof(keep));
+        sph_free(c);
+        memcpy(g_err, keep, sizeof(keep));
+        return st;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+sph_status sph_rhs(sph_ctx *c, const sph_rates *out)
+{
+    if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
+    if (c->n > 0 && (!out->ax || !out->ay || !out->az || !out->dudt || !out->drhodt || !out->rho ||
+                     !out->P || !out->D || !out->cs || !out->deps || !out->dR || !out->dS ||
+                     !out->ncount))
+        return fail(SPH_ERR_ARG, "a rate array is NULL");
+    if (c->timing) {
+        STATUS_TRY(ensure_slot(c));
+        c->slot_kind_step = 0;
+    }
+    DevState st = state_of(c, c->P.vx, c->P.vy, c->P.vz, c->P.S);
+    int nl = 0;
+    enqueue_rhs(c, st, rates_of(out), false, &nl);
+    if (c->timing) c->slot_used++;
+    CUDA_TRY(cudaGetLastError());
+    return SPH_OK;
+}
+
+sph_status sph_step(sph_ctx *c, double dt, int32_t nsteps)
+{
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(SPH_ERR_ARG, "bad dt or nsteps");
+    if (c->n == 0) {
+        c->steps += nsteps;
+        return SPH_OK;
+    }
+    if (!c->have_rates) {
+        DevState st = state_of(c, c->P.vx, c->P.vy, c->P.vz, c->P.S);
+        enqueue_rhs(c, st, c->r, false, nullptr);
+        c->have_rates = 1;
+    }
+    bool graph = c->opt.use_graph && c->stream != nullptr;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        if (c->timing) {
+            STATUS_TRY(ensure_slot(c));
+            c->slot_kind_step = 1;
+        }
+        if (graph) {
+            if (!c->gexec || c->gdt != dt || c->gtiming != c->timing) STATUS_TRY(capture_step(c, dt));
+            if (c->timing) {
+                for (int e = 0; e < 6; ++e)
+                    if (c->gev_nodes[e])
+                        CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->gev_nodes[e],
+                                                                      c->slots[c->slot_used].ev[e]));
+            }
+            CUDA_TRY(cudaGraphLaunch(c->gexec, c->stream));
+        } else {
+            int nl = 0;
+            enqueue_step(c, dt, false, &nl);
+            c->launches_per_step = nl;
+        }
+        if (c->timing) c->slot_used++;
+        c->steps++;
+        if (c->opt.totals_every > 0 && c->steps % c->opt.totals_every == 0) {
+            StepState ss = step_state_of(c);
+            launch_totals(ss, c->r.ncount, c->tot_partial, c->tot_out, c->stream);
+        }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return SPH_OK;
+}
+
+sph_status sph_sync(sph_ctx *c)
+{
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->n == 0) return SPH_OK;
+    int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, &c->s.sc->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        int zero = 0;
+        CUDA_TRY(cudaMemcpy(&c->s.sc->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        if (err & ERR_NONFINITE) return fail(SPH_ERR_NONFINITE, "non-finite position, velocity or h");
+        if (err & ERR_CAPACITY)
+            return fail(SPH_ERR_CAPACITY, "a neighbour list exceeded max_neighbors = %d", c->cap);
+        if (err & ERR_BOUNDS) return fail(SPH_ERR_BOUNDS, "index out of bounds");
+        if (err & ERR_TIMEOUT) return fail(SPH_ERR_TIMEOUT, "device wait timed out");
+    }
+    return SPH_OK;
+}
+
+sph_status sph_neighbors(sph_ctx *c, int64_t *offsets, int32_t *idx, int64_t cap)
+{
+    if (!c || !offsets || (cap > 0 && !idx) || cap < 0) return fail(SPH_ERR_ARG, "bad argument");
+    const int64_t n = c->n;
+    CUDA_TRY(cudaMemsetAsync(offsets, 0, (n + 1) * sizeof(int64_t), c->stream));
+    launch_export_counts(c->s, n, offsets + 1, c->stream);
+    launch_scan_i64(offsets, n + 1, c->stream);
+    int64_t total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (total > cap) return fail(SPH_ERR_CAPACITY, "neighbour lists hold %lld entries > cap %lld",
+                                 (long long)total, (long long)cap);
+    launch_export_fill(c->s, n, c->cap, offsets, idx, c->stream);
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaGetLastError());
+    return SPH_OK;
+}
+
+sph_status sph_totals(sph_ctx *c, double out[16])
+{
+    if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
+    StepState ss = step_state_of(c);
+    launch_totals(ss, c->have_rates ? c->r.ncount : nullptr, c->tot_partial, c->tot_out, c->stream);
+    CUDA_TRY(cudaMemcpyAsync(out, c->tot_out, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+sph_status sph_stats(sph_ctx *c, int64_t out[16])
+{
+    if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
+    DevScalars sc{};
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaMemcpy(&sc, c->s.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 16; ++k) out[k] = 0;
+    out[0] = (int64_t)sc.pairs_last;
+    out[1] = (int64_t)sc.pairs_total;
+    out[2] = (int64_t)sc.rhs_count;
+    out[3] = c->launches_per_step;
+    out[4] = c->nleaves;
+    out[5] = (int64_t)sc.rechecks;
+    out[6] = c->cap;
+    out[7] = c->lanes;
+    out[8] = (c->opt.use_graph && c->stream != nullptr) ? 1 : 0;
+    out[9] = c->steps;
+    out[10] = c->plan.passes;
+    out[11] = c->plan.key_bits_axis;
+    return SPH_OK;
+}
+
+sph_status sph_timing(sph_ctx *c, int32_t enable)
+{
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    c->timing = enable ? 1 : 0;
+    c->slot_used = 0;
+    return SPH_OK;
+}
+
+sph_status sph_timing_read(sph_ctx *c, double out[8])
+{
+    if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 8; ++k) out[k] = 0.0;
+    for (int k = 0; k < c->slot_used; ++k) {
+        float ms = 0.f;
+        TimingSlot &s = c->slots[k];
+        if (cudaEventElapsedTime(&ms, s.ev[3], s.ev[4]) == cudaSuccess) {
+            out[0] += ms;
+            out[1] += 1;
+        }
+        if (cudaEventElapsedTime(&ms, s.ev[2], s.ev[3]) == cudaSuccess) {
+            out[2] += ms;
+            out[3] += 1;
+        }
+        if (cudaEventElapsedTime(&ms, s.ev[0], s.ev[5]) == cudaSuccess) {
+            out[4] += ms;
+            out[5] += 1;
+        } else if (cudaEventElapsedTime(&ms, s.ev[1], s.ev[4]) == cudaSuccess) {
+            out[4] += ms;
+            out[5] += 1;
+        }
+        if (cudaEventElapsedTime(&ms, s.ev[1], s.ev[2]) == cudaSuccess) {
+            out[6] += ms;
+            out[7] += 1;
+        }
+    }
+    cudaGetLastError();
+    c->slot_used = 0;
+    return SPH_OK;
+}
+
+sph_status sph_state_size(sph_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return fail(SPH_ERR_ARG, "null argument");
+    *bytes = state_blob_size(c);
+    return SPH_OK;
+}
+
+sph_status sph_get_state(sph_ctx *c, void *host_buf, int64_t bytes)
+{
+    if (!c || !host_buf) return fail(SPH_ERR_ARG, "null argument");
+    if (bytes < state_blob_size(c)) return fail(SPH_ERR_ARG, "buffer too small");
+    const int64_t n = c->n;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    int64_t *hdr = (int64_t *)host_buf;
+    hdr[0] = 0x53504831;  // "SPH1"
+    hdr[1] = n;
+    hdr[2] = c->steps;
+    hdr[3] = c->have_rates;
+    hdr[4] = c->nstars;
+    hdr[5] = hdr[6] = hdr[7] = 0;
+    char *p = (char *)host_buf + 64;
+    auto get = [&](const void *src, size_t sz) -> sph_status {
+        if (src) CUDA_TRY(cudaMemcpy(p, src, sz, cudaMemcpyDeviceToHost));
+        else memset(p, 0, sz);
+        p += sz;
+        return SPH_OK;
+    };
+    const size_t d = n * sizeof(double);
+    const double *fields[11] = {c->P.x, c->P.y, c->P.z, c->P.vx, c->P.vy, c->P.vz,
+                                c->P.u, c->P.h, c->P.mu, c->P.Y0, c->P.eps_break};
+    for (const double *f : fields) STATUS_TRY(get(f, d));
+    STATUS_TRY(get(c->P.S, 6 * d));
+    for (const double *f : {c->r.ax, c->r.ay, c->r.az, c->r.dudt}) STATUS_TRY(get(f, d));
+    STATUS_TRY(get(c->r.dS, 6 * d));
+    STATUS_TRY(get(c->P.type, n));
+    STATUS_TRY(get(c->P.flags, n));
+    return SPH_OK;
+}
+
+sph_status sph_set_state(sph_ctx *c, const void *host_buf, int64_t bytes)
+{
+    if (!c || !host_buf) return fail(SPH_ERR_ARG, "null argument");
+    if (bytes < state_blob_size(c)) return fail(SPH_ERR_ARG, "buffer too small");
+    const int64_t n = c->n;
+    const int64_t *hdr = (const int64_t *)host_buf;
+    if (hdr[0] != 0x53504831 || hdr[1] != n || hdr[4] != c->nstars)
+        return fail(SPH_ERR_ARG, "checkpoint does not match this context");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const char *p = (const char *)host_buf + 64;
+    auto put = [&](void *dst, size_t sz) -> sph_status {
+        if (dst) CUDA_TRY(cudaMemcpy(dst, p, sz, cudaMemcpyHostToDevice));
+        p += sz;
+        return SPH_OK;
+    };
+    const size_t d = n * sizeof(double);
+    for (double *f : {c->P.x, c->P.y, c->P.z, c->P.vx, c->P.vy, c->P.vz, c->P.u, c->P.h, c->P.mu,
+                      c->P.Y0, c->P.eps_break})
+        STATUS_TRY(put(f, d));
+    STATUS_TRY(put(c->P.S, 6 * d));
+    for (double *f : {c->r.ax, c->r.ay, c->r.az, c->r.dudt}) STATUS_TRY(put(f, d));
+    STATUS_TRY(put(c->r.dS, 6 * d));
+    STATUS_TRY(put(c->P.type, n));
+    STATUS_TRY(put(c->P.flags, n));
+    c->steps = hdr[2];
+    c->have_rates = (int)hdr[3];
+    return SPH_OK;
+}
+
+void sph_free(sph_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(c);
+    for (auto &s : c->slots)
+        for (int e = 0; e < 6; ++e) cudaEventDestroy(s.ev[e]);
+    for (void *p : c->allocs) cudaFree(p);
+    cudaGetLastError();
+    delete c;
+}
+
+const char *sph_last_error(void) { return g_err; }
+
+}  // extern "C"

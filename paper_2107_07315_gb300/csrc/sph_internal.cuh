@@ -1,0 +1,168 @@
+// Internal declarations shared by the libsph translation units.
+//
+// Data layout in device memory (n particles, "sorted" = Morton order):
+//   caller order : the caller's state and rate buffers (borrowed).
+//   perm[n]      : sorted slot -> caller index (int32).
+//   xs,ys,zs,hs  : FP64 sorted positions and smoothing lengths.
+//   rec[n][4]    : float4 j-record per sorted particle:
+//                  0 (Xhi.x, Xhi.y, Xhi.z, h)  1 (Xlo.x, Xlo.y, Xlo.z, m)
+//                  2 (v.x, v.y, v.z, D)         3 (P/D^2, c_s, 1/D, 0)
+//                  Xhi + Xlo is the FP64 position split into an FP32 value
+//                  on a power-of-two grid and an FP32 remainder.
+//   rec64[n][3]  : double4_32a j-record of the FP64 path: (x,y,z,h), (m,vx,vy,vz),
+//                  (D, 1/D, P/D^2, c_s).
+//   sd2 / sd264  : S/D^2 per sorted particle, 2 float4 or 8 doubles.
+//   pp / pp64    : per-particle EoS values for the finalize step:
+//                  (rho, P, dP/drho, h_enth), (W~, c_s, D, 0).
+//   nbr[n*cap]   : neighbour list of each sorted particle (sorted indices,
+//                  ascending), ncnt[n] its length.
+//   tree nodes   : implicit binary tree over leaves of 8 consecutive sorted
+//                  particles of one star; node = float4 (lo.xyz, h_max) +
+//                  float4 (hi.xyz, star range packed in an int).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int kLeaf = 8;          // particles per tree leaf
+constexpr int kMaxLevels = 32;
+constexpr int kTreeBlock = 256;   // leaves per block in the tree kernel (2^8)
+constexpr int kTreeBlockLevels = 8;
+
+// Device error word bits.
+enum : int {
+    ERR_CAPACITY = 1,
+    ERR_NONFINITE = 2,
+    ERR_BOUNDS = 4,
+    ERR_TIMEOUT = 8,
+};
+
+// Device scalars shared between kernels of one right-hand side.
+struct DevScalars {
+    unsigned long long bbox_lo[3];   // order-preserving encodings of doubles
+    unsigned long long bbox_hi[3];
+    double grid;                     // Xhi grid spacing (power of two)
+    double eps_abs;                  // absolute slack for tree pruning
+    int err;                         // ERR_* bits
+    int tree_done;                   // block counter of the tree kernel
+    unsigned long long pairs_last;   // ordered pairs of the last RHS
+    unsigned long long pairs_total;
+    unsigned long long rechecks;     // marginal FP64 predicate evaluations
+    unsigned long long rhs_count;
+};
+
+struct DevState {
+    int64_t n;
+    const double *x, *y, *z;
+    const double *vx, *vy, *vz;      // velocity used by the RHS (may be predicted)
+    const double *S;                 // stress used by the RHS (may be predicted)
+    const double *h, *m, *mu;
+    const uint8_t *type;
+    const int32_t *star;             // may be null
+};
+
+struct DevEos {
+    const double *K, *Gamma;
+};
+
+struct DevMaterial {
+    double alpha_av, beta_av, eta2;
+    int jaumann, yield_mode, break_stress, break_zero_S;
+};
+
+struct DevMetric {
+    int kind, nstars, nr, pressure_form;
+    const double *r_max, *M, *center;
+    const double *tab;   // [nstars][nr][4]: alpha, dalpha, psi4, dpsi4
+    const float *tabf;   // FP32 copy
+};
+
+struct DevRates {
+    double *ax, *ay, *az, *dudt, *drhodt, *rho, *P, *D, *cs;
+    double *deps, *dR, *dS;
+    int32_t *ncount;
+};
+
+struct TreeLevels {
+    int nlevels;
+    int count[kMaxLevels];
+    int offset[kMaxLevels];
+};
+
+// Scratch of one context (device pointers).
+struct Scratch {
+    int32_t *perm;
+    unsigned long long *keys[2];
+    uint32_t *vals[2];
+    uint32_t *hist;           // [passes][256][nblocks]
+    double *xs, *ys, *zs, *hs;
+    uint8_t *tys;             // sorted type
+    float4 *rec;              // [n][4]
+    double4_32a *rec64;           // [n][3]
+    float4 *sd2;              // [n][2]
+    double *sd264;            // [n][8]
+    float4 *pp;               // [n][2]
+    double *pp64;             // [n][8]
+    int32_t *nbr;             // [n][cap]
+    int32_t *ncnt;            // [n]
+    float4 *nodes;            // [total nodes][2]
+    int32_t *leaf_start;      // [nleaves+1]
+    int32_t *leaf_star;       // [nleaves]
+    int32_t *leaf_of;         // [n] leaf of each sorted slot
+    double *bbox_partial;     // [6 * 304]
+    unsigned int *bbox_done;  // block counter of the bounding-box kernel
+    DevScalars *sc;
+};
+
+// Launch helpers implemented in sph_build.cu.
+struct SortPlan {
+    int key_bits_axis;  // Morton bits per axis
+    int star_bits;
+    int passes;         // 8-bit digit passes
+    int ipt;            // items per thread in sort kernels
+    int nblocks;        // sort tiles
+};
+
+constexpr int kBoxBlocksMax = 304;
+
+void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
+                  const TreeLevels &tl, int nleaves, int cap, int fp64_records,
+                  cudaStream_t stream, int *nlaunch);
+
+void launch_density(const DevState &st, const Scratch &s, const DevEos &eos,
+                    const DevMetric &g, const DevRates &out, int cap, int lanes, int fp64,
+                    cudaStream_t stream);
+
+void launch_force(const DevState &st, const Scratch &s, const DevEos &eos,
+                  const DevMaterial &mat, const DevMetric &g, const DevRates &out, int cap,
+                  int lanes, int fp64, cudaStream_t stream);
+
+// Step kernels (sph_step.cu).
+struct StepState {
+    int64_t n;
+    double *x, *y, *z, *vx, *vy, *vz, *u, *h, *S;
+    const double *m;
+    uint8_t *type, *flags;
+    const int32_t *star;
+    double *mu, *Y0, *eps_break;
+    double *vp, *Sp;  // predicted velocity (3n) and stress (6n)
+};
+
+void launch_kick_drift(const StepState &s, const DevRates &r, double dt, cudaStream_t st);
+void launch_kick_return(const StepState &s, const DevRates &r, const DevEos &eos,
+                        const DevMaterial &mat, double dt, int h_nmin, int h_nmax,
+                        cudaStream_t st);
+constexpr int kTotalsBlocks = 256;
+void launch_totals(const StepState &s, const int32_t *ncount, double *partial, double *out,
+                   cudaStream_t st);
+void launch_export_counts(const Scratch &s, int64_t n, int64_t *offsets_plus1,
+                          cudaStream_t st);
+void launch_export_fill(const Scratch &s, int64_t n, int cap, const int64_t *offsets,
+                        int32_t *idx, cudaStream_t st);
+void launch_scan_i64(int64_t *data, int64_t n, cudaStream_t st);
+
+}  // namespace sph

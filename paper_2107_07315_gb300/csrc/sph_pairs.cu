@@ -1,0 +1,593 @@
+// Pair kernels of the right-hand side.
+//
+// Each particle's exact neighbour list (built by the neighbour search) is
+// shared by LPI consecutive threads of a warp; thread `sub` of the group
+// takes entries sub, sub+LPI, ...  and the group's partial sums are combined
+// with xor shuffles (fixed order, deterministic).
+//
+//   density : D_a = m_a W(0,h_a) + sum_b m_b W(r_ab, h_ab)    (Sec. I.C, D from
+//             the "standard formula"), then the equation of state
+//             (Eq. poly_eos, Sec. II.A) and rho = D/(sqrt(gamma) W).
+//   force   : pair sums of Eqs. solid1, solid2, solid3, solid5, solid6 with
+//             Monaghan viscosity, then per particle: strain and rotation
+//             rates, the stress rate of Eq. solid4, the elastic work term of
+//             Eq. solid3 and the background force of Sec. I.C.
+//
+// Mixed precision: pair arithmetic in FP32 on the two-float position split
+// (exact Xhi differences plus FP32 remainders), compensated (Kahan) sums for
+// D and du/dt, per-particle terms in FP32; FP64 stays with the state.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr float kInvPiF = 0.318309886183790671538f;
+
+template <typename T>
+struct MetricPt {
+    T alpha, dalpha, psi4, dpsi4;
+};
+
+// Static isotropic background (Sec. I.C): linear interpolation of the tables
+// on uniform nodes 0..r_max, exterior Schwarzschild in isotropic form beyond.
+template <typename T>
+__device__ __forceinline__ MetricPt<T> metric_radial(const DevMetric &g, int s, T r)
+{
+    MetricPt<T> p;
+    T rmax = (T)g.r_max[s];
+    if (r <= rmax) {
+        T dr = rmax / (T)(g.nr - 1);
+        T t = r / dr;
+        int i = (int)floor(t);
+        i = max(0, min(i, g.nr - 2));
+        T f = t - (T)i;
+        int64_t o = ((int64_t)s * g.nr + i) * 4;
+        T a0, a1, b0, b1, c0, c1, d0, d1;
+        if (sizeof(T) == 8) {
+            a0 = (T)g.tab[o + 0]; b0 = (T)g.tab[o + 1]; c0 = (T)g.tab[o + 2]; d0 = (T)g.tab[o + 3];
+            a1 = (T)g.tab[o + 4]; b1 = (T)g.tab[o + 5]; c1 = (T)g.tab[o + 6]; d1 = (T)g.tab[o + 7];
+        } else {
+            a0 = (T)g.tabf[o + 0]; b0 = (T)g.tabf[o + 1]; c0 = (T)g.tabf[o + 2]; d0 = (T)g.tabf[o + 3];
+            a1 = (T)g.tabf[o + 4]; b1 = (T)g.tabf[o + 5]; c1 = (T)g.tabf[o + 6]; d1 = (T)g.tabf[o + 7];
+        }
+        p.alpha = a0 + f * (a1 - a0);
+        p.dalpha = b0 + f * (b1 - b0);
+        p.psi4 = c0 + f * (c1 - c0);
+        p.dpsi4 = d0 + f * (d1 - d0);
+    } else {
+        T M = (T)g.M[s];
+        T k = M / ((T)2 * r);
+        T psi = (T)1 + k;
+        T dk = -k / r;
+        p.alpha = ((T)1 - k) / ((T)1 + k);
+        p.dalpha = -(T)2 * dk / (((T)1 + k) * ((T)1 + k));
+        p.psi4 = psi * psi * psi * psi;
+        p.dpsi4 = (T)4 * psi * psi * psi * dk;
+    }
+    return p;
+}
+
+// Metric value and Cartesian gradients at sorted particle i.
+template <typename T>
+__device__ __forceinline__ void metric_at(const DevMetric &g, int s, double x, double y, double z,
+                                          T &alpha, T ga[3], T &psi4, T gq[3])
+{
+    T c[3] = {(T)(x - g.center[3 * s + 0]), (T)(y - g.center[3 * s + 1]),
+              (T)(z - g.center[3 * s + 2])};
+    T r = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    MetricPt<T> p = metric_radial<T>(g, s, r);
+    T inv = r > (T)0 ? (T)1 / r : (T)0;
+    alpha = p.alpha;
+    psi4 = p.psi4;
+    for (int k = 0; k < 3; ++k) {
+        ga[k] = p.dalpha * c[k] * inv;
+        gq[k] = p.dpsi4 * c[k] * inv;
+    }
+}
+
+// Equation of state and the per-particle factors of the pair sums.
+template <typename T>
+struct Prep {
+    T rho, P, cP, cs, henth, Wt;
+};
+
+template <typename T>
+__device__ __forceinline__ Prep<T> eos_prep(const DevEos &eos, const DevMetric &g, int star,
+                                            T D, T vx, T vy, T vz, double x, double y, double z)
+{
+    Prep<T> p;
+    T K = (T)eos.K[star], G = (T)eos.Gamma[star];
+    bool metric = g.kind == 1;
+    if (metric) {
+        T al, ga[3], q4, gq[3];
+        metric_at<T>(g, star, x, y, z, al, ga, q4, gq);
+        T v2 = vx * vx + vy * vy + vz * vz;
+        T vv = q4 * v2 / (al * al);              // v^i v_i, v^i = xdot^i/alpha
+        T Wl = (T)1 / sqrt((T)1 - vv);           // Lorentz factor
+        T sqrtg = q4 * sqrt(q4);                 // psi^6
+        p.rho = D / (sqrtg * Wl);
+        p.Wt = (T)1 / sqrt(al * al - q4 * v2);   // generalised Lorentz factor
+    } else {
+        p.rho = D;
+        p.Wt = (T)1;
+    }
+    T rg1 = pow(p.rho, G - (T)1);
+    p.P = K * p.rho * rg1;
+    T ue = K * rg1 / (G - (T)1);
+    p.cP = G * K * rg1;
+    p.henth = (T)1 + ue + p.P / p.rho;
+    p.cs = metric ? sqrt(p.cP / p.henth) : sqrt(p.cP);
+    return p;
+}
+
+// ------------------------------------------------------------------ density
+template <int LPI>
+__global__ void __launch_bounds__(128)
+k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRates out, int cap)
+{
+    const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
+    const bool valid = i < n;
+    const int cnt = valid ? s.ncnt[i] : 0;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        a0 = s.rec[i * 4 + 0];
+        a1 = s.rec[i * 4 + 1];
+    }
+    float sum = 0.f, comp = 0.f;
+    const int32_t *list = s.nbr + i * (int64_t)cap;
+    for (int k = sub; k < cnt; k += LPI) {
+        int j = list[k];
+        float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
+        float dx = (a0.x - q0.x) + (a1.x - q1.x);
+        float dy = (a0.y - q0.y) + (a1.y - q1.y);
+        float dz = (a0.z - q0.z) + (a1.z - q1.z);
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float hab = 0.5f * (a0.w + q0.w);
+        float hinv = __frcp_rn(hab);
+        float q = sqrtf(r2) * hinv;
+        float sig = hinv * hinv * hinv * kInvPiF;
+        float t = 2.f - q;
+        float W = q < 1.f ? sig * fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.f) : sig * 0.25f * t * t * t;
+        float term = q1.w * W;
+        float y = term - comp;
+        float tt = sum + y;
+        comp = (tt - sum) - y;
+        sum = tt;
+    }
+    for (int o = LPI / 2; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        comp += __shfl_xor_sync(0xffffffffu, comp, o);
+    }
+    if (!valid) return;
+    float hi = a0.w;
+    float self = a1.w * kInvPiF / (hi * hi * hi);
+    float D = self + (sum - comp);
+    int c = s.perm[i];
+    int star = st.star ? st.star[c] : 0;
+    float vx = (float)st.vx[c], vy = (float)st.vy[c], vz = (float)st.vz[c];
+    Prep<float> p = eos_prep<float>(eos, g, star, D, vx, vy, vz, s.xs[i], s.ys[i], s.zs[i]);
+    if (sub != 0) return;
+    float invD = 1.f / D;
+    float PD2 = p.P * invD * invD;
+    s.rec[i * 4 + 2] = make_float4(vx, vy, vz, D);
+    s.rec[i * 4 + 3] = make_float4(PD2, p.cs, invD, 0.f);
+    if (s.tys[i] == 1) {
+        const int64_t N = st.n;
+        float f = invD * invD;
+        s.sd2[i * 2 + 0] = make_float4((float)st.S[c] * f, (float)st.S[N + c] * f,
+                                       (float)st.S[2 * N + c] * f, (float)st.S[3 * N + c] * f);
+        s.sd2[i * 2 + 1] = make_float4((float)st.S[4 * N + c] * f, (float)st.S[5 * N + c] * f,
+                                       0.f, 0.f);
+    } else {
+        s.sd2[i * 2 + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s.sd2[i * 2 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    s.pp[i * 2 + 0] = make_float4(p.rho, p.P, p.cP, p.henth);
+    s.pp[i * 2 + 1] = make_float4(p.Wt, p.cs, D, 0.f);
+    out.D[c] = D;
+    out.rho[c] = p.rho;
+    out.P[c] = p.P;
+    out.cs[c] = p.cs;
+    out.ncount[c] = cnt;
+}
+
+template <int LPI>
+__global__ void __launch_bounds__(128)
+k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRates out, int cap)
+{
+    const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
+    const bool valid = i < n;
+    const int cnt = valid ? s.ncnt[i] : 0;
+    double4_32a a0 = make_double4_32a(0, 0, 0, 1);
+    double mi = 0.0;
+    if (valid) {
+        a0 = s.rec64[i * 3 + 0];
+        mi = s.rec64[i * 3 + 1].x;
+    }
+    double sum = 0.0;
+    const int32_t *list = s.nbr + i * (int64_t)cap;
+    for (int k = sub; k < cnt; k += LPI) {
+        int j = list[k];
+        double4_32a q0 = s.rec64[(int64_t)j * 3 + 0];
+        double mj = s.rec64[(int64_t)j * 3 + 1].x;
+        double dx = a0.x - q0.x, dy = a0.y - q0.y, dz = a0.z - q0.z;
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double hab = 0.5 * (a0.w + q0.w);
+        double q = r / hab;
+        double sig = 1.0 / (kPi * hab * hab * hab);
+        double W;
+        if (q < 1.0) W = sig * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+        else {
+            double t = 2.0 - q;
+            W = sig * 0.25 * t * t * t;
+        }
+        sum += mj * W;
+    }
+    for (int o = LPI / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (!valid) return;
+    double hi = a0.w;
+    double D = mi / (kPi * hi * hi * hi) + sum;
+    int c = s.perm[i];
+    int star = st.star ? st.star[c] : 0;
+    double vx = st.vx[c], vy = st.vy[c], vz = st.vz[c];
+    Prep<double> p = eos_prep<double>(eos, g, star, D, vx, vy, vz, a0.x, a0.y, a0.z);
+    if (sub != 0) return;
+    double invD = 1.0 / D;
+    double PD2 = p.P / (D * D);
+    s.rec64[i * 3 + 1] = make_double4_32a(mi, vx, vy, vz);
+    s.rec64[i * 3 + 2] = make_double4_32a(D, invD, PD2, p.cs);
+    double *sd = s.sd264 + i * 8;
+    const int64_t N = st.n;
+    bool solid = s.tys[i] == 1;
+    for (int k = 0; k < 6; ++k) sd[k] = solid ? st.S[k * N + c] / (D * D) : 0.0;
+    double *q = s.pp64 + i * 8;
+    q[0] = p.rho; q[1] = p.P; q[2] = p.cP; q[3] = p.henth; q[4] = p.Wt; q[5] = p.cs; q[6] = D;
+    out.D[c] = D;
+    out.rho[c] = p.rho;
+    out.P[c] = p.P;
+    out.cs[c] = p.cs;
+    out.ncount[c] = cnt;
+}
+
+// -------------------------------------------------------------- finalize
+// Strain rate, rotation rate, stress rate (Eq. solid4), elastic work
+// (Eq. solid3) and acceleration, from the reduced pair sums of particle i.
+//   G[p][q] = sum_b m_b v_ba^p d_q W_ab  (so eps = (G+G^T)/2D, R = (G-G^T)/2D)
+template <typename T>
+__device__ __forceinline__ void finalize(int64_t i, int c, int64_t N, const DevState &st,
+                                         const DevMaterial &mat, const DevMetric &g, int star,
+                                         bool solid, T D, const T aP[3], const T aX[3], T du,
+                                         T dD, const T G[3][3], T rho, T cP, T henth, T Wt,
+                                         T vx, T vy, T vz, double x, double y, double z,
+                                         const DevRates &out)
+{
+    T drhodt = D * dD;
+    T eps[3][3], R[3][3], dS[3][3];
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+            eps[p][q] = (T)0;
+            R[p][q] = (T)0;
+            dS[p][q] = (T)0;
+        }
+    if (solid) {
+        T inv2D = (T)1 / ((T)2 * D);
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) {
+                eps[p][q] = (G[p][q] + G[q][p]) * inv2D;
+                R[p][q] = (G[p][q] - G[q][p]) * inv2D;
+            }
+        T tr3 = (eps[0][0] + eps[1][1] + eps[2][2]) / (T)3;
+        T S6[6];
+        for (int k = 0; k < 6; ++k) S6[k] = (T)st.S[k * N + c];
+        T Sm[3][3] = {{S6[0], S6[3], S6[4]}, {S6[3], S6[1], S6[5]}, {S6[4], S6[5], S6[2]}};
+        T mu = (T)st.mu[c];
+        T Seps = (T)0;
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) {
+                T RS = R[p][0] * Sm[0][q] + R[p][1] * Sm[1][q] + R[p][2] * Sm[2][q];
+                T SR = Sm[p][0] * R[0][q] + Sm[p][1] * R[1][q] + Sm[p][2] * R[2][q];
+                T J = mat.jaumann == 1 ? SR - RS : RS - SR;
+                dS[p][q] = (T)2 * mu * (eps[p][q] - (p == q ? tr3 : (T)0)) + J;
+                Seps += Sm[p][q] * eps[p][q];
+            }
+        du += Seps / D;
+    }
+    T acc[3];
+    if (g.kind == 1) {
+        T al, ga[3], q4, gq[3];
+        metric_at<T>(g, star, x, y, z, al, ga, q4, gq);
+        T xd[3] = {vx, vy, vz};
+        T C = g.pressure_form == 1 ? (T)1 / (Wt * rho * henth) : (T)1 / (Wt * Wt * rho * henth);
+        T gradP[3] = {-D * aP[0], -D * aP[1], -D * aP[2]};
+        T dtP = cP * (rho / D) * drhodt - (xd[0] * gradP[0] + xd[1] * gradP[1] + xd[2] * gradP[2]);
+        T v2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+        T vq = xd[0] * gq[0] + xd[1] * gq[1] + xd[2] * gq[2];
+        T va = xd[0] * ga[0] + xd[1] * ga[1] + xd[2] * ga[2];
+        T gam0 = -(T)2 * al * va;
+        for (int k = 0; k < 3; ++k) {
+            T gamk = xd[k] * vq + al * ga[k] - (T)0.5 * gq[k] * v2;
+            acc[k] = -(C * gradP[k] + gamk) / q4 - (xd[k] / (al * al)) * (C * dtP + gam0) + aX[k];
+        }
+    } else {
+        for (int k = 0; k < 3; ++k) acc[k] = aP[k] + aX[k];
+    }
+    out.ax[c] = (double)acc[0];
+    out.ay[c] = (double)acc[1];
+    out.az[c] = (double)acc[2];
+    out.dudt[c] = (double)du;
+    out.drhodt[c] = (double)drhodt;
+    const int ci[6] = {0, 1, 2, 0, 0, 1}, cj[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) {
+        out.deps[k * N + c] = (double)eps[ci[k]][cj[k]];
+        out.dS[k * N + c] = (double)dS[ci[k]][cj[k]];
+    }
+    out.dR[c] = (double)R[0][1];
+    out.dR[N + c] = (double)R[0][2];
+    out.dR[2 * N + c] = (double)R[1][2];
+}
+
+// ------------------------------------------------------------------- force
+template <int LPI>
+__global__ void __launch_bounds__(128)
+k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
+              DevRates out, int cap)
+{
+    (void)eos;
+    const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
+    const bool valid = i < n;
+    const int cnt = valid ? s.ncnt[i] : 0;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = a0, a2 = make_float4(0.f, 0.f, 0.f, 1.f),
+           a3 = make_float4(0.f, 0.f, 1.f, 0.f), as0 = make_float4(0.f, 0.f, 0.f, 0.f), as1 = as0;
+    bool solid_i = false;
+    if (valid) {
+        a0 = s.rec[i * 4 + 0];
+        a1 = s.rec[i * 4 + 1];
+        a2 = s.rec[i * 4 + 2];
+        a3 = s.rec[i * 4 + 3];
+        solid_i = s.tys[i] == 1;
+        if (solid_i) {
+            as0 = s.sd2[i * 2 + 0];
+            as1 = s.sd2[i * 2 + 1];
+        }
+    }
+    const float alpha_av = (float)mat.alpha_av, beta_av = (float)mat.beta_av;
+    const float eta2 = (float)mat.eta2;
+    float aP0 = 0.f, aP1 = 0.f, aP2 = 0.f, aX0 = 0.f, aX1 = 0.f, aX2 = 0.f;
+    float du = 0.f, duc = 0.f, dD = 0.f;
+    float G00 = 0.f, G01 = 0.f, G02 = 0.f, G10 = 0.f, G11 = 0.f, G12 = 0.f, G20 = 0.f, G21 = 0.f,
+          G22 = 0.f;
+    const int32_t *list = s.nbr + i * (int64_t)cap;
+    for (int k = sub; k < cnt; k += LPI) {
+        const int j = list[k];
+        const float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
+        const float4 q2 = s.rec[(int64_t)j * 4 + 2], q3 = s.rec[(int64_t)j * 4 + 3];
+        const bool solid_j = s.tys[j] == 1;
+        float dx = (a0.x - q0.x) + (a1.x - q1.x);
+        float dy = (a0.y - q0.y) + (a1.y - q1.y);
+        float dz = (a0.z - q0.z) + (a1.z - q1.z);
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float r2c = fmaxf(r2, 1.17549435e-38f);
+        float rinv = rsqrtf(r2c);
+        float r = r2c * rinv;
+        float hab = 0.5f * (a0.w + q0.w);
+        float hinv = __frcp_rn(hab);
+        float q = r * hinv;
+        float hinv2 = hinv * hinv;
+        float s5 = hinv2 * hinv2 * hinv * kInvPiF;
+        float t = 2.f - q;
+        float gW = q < 1.f ? s5 * fmaf(2.25f, q, -3.f) : -0.75f * s5 * t * t * hab * rinv;
+        float w = q1.w * gW;
+        float dvx = a2.x - q2.x, dvy = a2.y - q2.y, dvz = a2.z - q2.z;
+        float vdx = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
+        float Pi = 0.f;
+        if (vdx < 0.f) {
+            float mu = hab * vdx / fmaf(eta2 * hab, hab, r2);
+            float cbar = 0.5f * (a3.y + q3.y);
+            Pi = fmaf(-alpha_av * cbar, mu, beta_av * mu * mu) * (2.f / (a2.w + q2.w));
+        }
+        float fp = (a3.x + q3.x) * w;
+        float fv = Pi * w;
+        aP0 = fmaf(-fp, dx, aP0);
+        aP1 = fmaf(-fp, dy, aP1);
+        aP2 = fmaf(-fp, dz, aP2);
+        aX0 = fmaf(-fv, dx, aX0);
+        aX1 = fmaf(-fv, dy, aX1);
+        aX2 = fmaf(-fv, dz, aX2);
+        float vw = vdx * w;
+        float term = fmaf(0.5f, Pi, a3.x) * vw;
+        float yk = term - duc;
+        float tk = du + yk;
+        duc = (tk - du) - yk;
+        du = tk;
+        dD = fmaf(vw, q3.z, dD);
+        if (solid_i || solid_j) {
+            float wx = w * dx, wy = w * dy, wz = w * dz;
+            float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+            if (solid_j) {
+                b0 = s.sd2[(int64_t)j * 2 + 0];
+                b1 = s.sd2[(int64_t)j * 2 + 1];
+            }
+            float Txx = as0.x + b0.x, Tyy = as0.y + b0.y, Tzz = as0.z + b0.z;
+            float Txy = as0.w + b0.w, Txz = as1.x + b1.x, Tyz = as1.y + b1.y;
+            aX0 = fmaf(Txx, wx, fmaf(Txy, wy, fmaf(Txz, wz, aX0)));
+            aX1 = fmaf(Txy, wx, fmaf(Tyy, wy, fmaf(Tyz, wz, aX1)));
+            aX2 = fmaf(Txz, wx, fmaf(Tyz, wy, fmaf(Tzz, wz, aX2)));
+            if (solid_i) {
+                G00 = fmaf(-dvx, wx, G00); G01 = fmaf(-dvx, wy, G01); G02 = fmaf(-dvx, wz, G02);
+                G10 = fmaf(-dvy, wx, G10); G11 = fmaf(-dvy, wy, G11); G12 = fmaf(-dvy, wz, G12);
+                G20 = fmaf(-dvz, wx, G20); G21 = fmaf(-dvz, wy, G21); G22 = fmaf(-dvz, wz, G22);
+            }
+        }
+    }
+#define SPH_RED(v) v += __shfl_xor_sync(0xffffffffu, v, o)
+    for (int o = LPI / 2; o > 0; o >>= 1) {
+        SPH_RED(aP0); SPH_RED(aP1); SPH_RED(aP2); SPH_RED(aX0); SPH_RED(aX1); SPH_RED(aX2);
+        SPH_RED(du); SPH_RED(duc); SPH_RED(dD);
+        SPH_RED(G00); SPH_RED(G01); SPH_RED(G02); SPH_RED(G10); SPH_RED(G11); SPH_RED(G12);
+        SPH_RED(G20); SPH_RED(G21); SPH_RED(G22);
+    }
+#undef SPH_RED
+    if (!valid || sub != 0) return;
+    const int c = s.perm[i];
+    const int star = st.star ? st.star[c] : 0;
+    const float4 p0 = s.pp[i * 2 + 0], p1 = s.pp[i * 2 + 1];
+    float aP[3] = {aP0, aP1, aP2}, aX[3] = {aX0, aX1, aX2};
+    float G[3][3] = {{G00, G01, G02}, {G10, G11, G12}, {G20, G21, G22}};
+    finalize<float>(i, c, st.n, st, mat, g, star, solid_i, a2.w, aP, aX, du - duc, dD, G, p0.x,
+                    p0.z, p0.w, p1.x, a2.x, a2.y, a2.z, s.xs[i], s.ys[i], s.zs[i], out);
+}
+
+template <int LPI>
+__global__ void __launch_bounds__(64)
+k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
+             DevRates out, int cap)
+{
+    (void)eos;
+    const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
+    const bool valid = i < n;
+    const int cnt = valid ? s.ncnt[i] : 0;
+    double4_32a a0 = make_double4_32a(0, 0, 0, 1), a1 = make_double4_32a(0, 0, 0, 0),
+            a2 = make_double4_32a(1, 1, 0, 0);
+    double sa[6] = {0, 0, 0, 0, 0, 0};
+    bool solid_i = false;
+    if (valid) {
+        a0 = s.rec64[i * 3 + 0];
+        a1 = s.rec64[i * 3 + 1];
+        a2 = s.rec64[i * 3 + 2];
+        solid_i = s.tys[i] == 1;
+        if (solid_i)
+            for (int k = 0; k < 6; ++k) sa[k] = s.sd264[i * 8 + k];
+    }
+    double aP[3] = {0, 0, 0}, aX[3] = {0, 0, 0}, du = 0.0, dD = 0.0;
+    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const int32_t *list = s.nbr + i * (int64_t)cap;
+    for (int k = sub; k < cnt; k += LPI) {
+        const int j = list[k];
+        const double4_32a q0 = s.rec64[(int64_t)j * 3 + 0], q1 = s.rec64[(int64_t)j * 3 + 1];
+        const double4_32a q2 = s.rec64[(int64_t)j * 3 + 2];
+        const bool solid_j = s.tys[j] == 1;
+        double dx[3] = {a0.x - q0.x, a0.y - q0.y, a0.z - q0.z};
+        double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+        double r = sqrt(r2);
+        double hab = 0.5 * (a0.w + q0.w);
+        double gW = 0.0;
+        if (r > 0.0) {
+            double q = r / hab;
+            double sig = 1.0 / (kPi * hab * hab * hab);
+            double dW;
+            if (q < 1.0) dW = (sig / hab) * (-3.0 * q + 2.25 * q * q);
+            else {
+                double t = 2.0 - q;
+                dW = -(sig / hab) * 0.75 * t * t;
+            }
+            gW = dW / r;
+        }
+        double w = q1.x * gW;
+        double dv[3] = {a1.y - q1.y, a1.z - q1.z, a1.w - q1.w};
+        double vdx = dv[0] * dx[0] + dv[1] * dx[1] + dv[2] * dx[2];
+        double Pi = 0.0;
+        if (vdx < 0.0) {
+            double mu = hab * vdx / (r2 + mat.eta2 * hab * hab);
+            double cbar = 0.5 * (a2.w + q2.w);
+            double Dbar = 0.5 * (a2.x + q2.x);
+            Pi = (-mat.alpha_av * cbar * mu + mat.beta_av * mu * mu) / Dbar;
+        }
+        double fp = (a2.z + q2.z) * w, fv = Pi * w;
+        for (int d = 0; d < 3; ++d) {
+            aP[d] -= fp * dx[d];
+            aX[d] -= fv * dx[d];
+        }
+        double vw = vdx * w;
+        du += (a2.z + 0.5 * Pi) * vw;
+        dD += vw * q2.y;
+        if (solid_i || solid_j) {
+            double wd[3] = {w * dx[0], w * dx[1], w * dx[2]};
+            double sb[6] = {0, 0, 0, 0, 0, 0};
+            if (solid_j)
+                for (int kk = 0; kk < 6; ++kk) sb[kk] = s.sd264[(int64_t)j * 8 + kk];
+            double T[3][3] = {{sa[0] + sb[0], sa[3] + sb[3], sa[4] + sb[4]},
+                              {sa[3] + sb[3], sa[1] + sb[1], sa[5] + sb[5]},
+                              {sa[4] + sb[4], sa[5] + sb[5], sa[2] + sb[2]}};
+            for (int p = 0; p < 3; ++p) aX[p] += T[p][0] * wd[0] + T[p][1] * wd[1] + T[p][2] * wd[2];
+            if (solid_i)
+                for (int p = 0; p < 3; ++p)
+                    for (int q = 0; q < 3; ++q) G[p][q] -= dv[p] * wd[q];
+        }
+    }
+    for (int o = LPI / 2; o > 0; o >>= 1) {
+        for (int d = 0; d < 3; ++d) {
+            aP[d] += __shfl_xor_sync(0xffffffffu, aP[d], o);
+            aX[d] += __shfl_xor_sync(0xffffffffu, aX[d], o);
+        }
+        du += __shfl_xor_sync(0xffffffffu, du, o);
+        dD += __shfl_xor_sync(0xffffffffu, dD, o);
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) G[p][q] += __shfl_xor_sync(0xffffffffu, G[p][q], o);
+    }
+    if (!valid || sub != 0) return;
+    const int c = s.perm[i];
+    const int star = st.star ? st.star[c] : 0;
+    const double *pp = s.pp64 + i * 8;
+    finalize<double>(i, c, st.n, st, mat, g, star, solid_i, a2.x, aP, aX, du, dD, G, pp[0],
+                     pp[2], pp[3], pp[4], a1.y, a1.z, a1.w, a0.x, a0.y, a0.z, out);
+}
+
+}  // namespace
+
+void launch_density(const DevState &st, const Scratch &s, const DevEos &eos, const DevMetric &g,
+                    const DevRates &out, int cap, int lanes, int fp64, cudaStream_t stream)
+{
+    const int T = 128;
+    int64_t n = st.n;
+    if (fp64) {
+        if (lanes == 4) {
+            k_density_fp64<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos, g,
+                                                                                 out, cap);
+        } else {
+            k_density_fp64<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos, g,
+                                                                                 out, cap);
+        }
+    } else {
+        if (lanes == 4) {
+            k_density_mixed<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos,
+                                                                                  g, out, cap);
+        } else {
+            k_density_mixed<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos,
+                                                                                  g, out, cap);
+        }
+    }
+}
+
+void launch_force(const DevState &st, const Scratch &s, const DevEos &eos, const DevMaterial &mat,
+                  const DevMetric &g, const DevRates &out, int cap, int lanes, int fp64,
+                  cudaStream_t stream)
+{
+    int64_t n = st.n;
+    if (fp64) {
+        const int T = 64;
+        if (lanes == 4) {
+            k_force_fp64<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos, mat,
+                                                                               g, out, cap);
+        } else {
+            k_force_fp64<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos, mat,
+                                                                               g, out, cap);
+        }
+    } else {
+        const int T = 128;
+        if (lanes == 4) {
+            k_force_mixed<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos, mat,
+                                                                                g, out, cap);
+        } else {
+            k_force_mixed<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos, mat,
+                                                                                g, out, cap);
+        }
+    }
+}
+
+}  // namespace sph

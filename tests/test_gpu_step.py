@@ -1,0 +1,162 @@
+"""Time stepping through the C ABI: integrator, yield, damage, h update,
+totals, CUDA-graph replay and checkpoint/resume, against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2107_07315_gb300 import inputs as I
+from paper_2107_07315_gb300 import sph
+
+pytestmark = pytest.mark.gpu
+MAT = dict(I.DEFAULT_MATERIAL)
+KEYS = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "S")
+
+
+from _parity import stream
+
+
+def _ctx(dev, eos, mat, metric, prec, options=None):
+    torch.cuda.synchronize()
+    return sph.sph_init(dev, eos, mat, metric, prec, options, stream=stream().cuda_stream)
+
+
+def _run(st, eos, metric, mat, prec, dt, nsteps, options=None):
+    dev = sph.device_state(st)
+    ctx = _ctx(dev, eos, mat, metric, prec, options)
+    sph.sph_step(ctx, dt, nsteps)
+    sph.sph_sync(ctx)
+    torch.cuda.synchronize()
+    return sph.to_numpy(dev), ctx, dev
+
+
+def _close(a, b, rel, keys=KEYS):
+    for k in keys:
+        x, y = np.asarray(a[k], np.float64), np.asarray(b[k], np.float64)
+        scale = max(np.abs(y).max(), 1e-300)
+        assert np.abs(x - y).max() <= rel * scale, (k, np.abs(x - y).max() / scale)
+
+
+def test_cube_ten_steps_fp64():
+    # config 0: 10 steps of dt = 1e-3 on the 16^3 elastic cube
+    st, eos, _, _ = I.cube_state()
+    g, ctx, _ = _run(st, eos, None, MAT, sph.SPH_FP64, 1e-3, 10)
+    o, _ = oracle.step(st, eos, MAT, None, 1e-3, 10)
+    _close(g, o, 1e-12)
+    assert np.array_equal(g["flags"], o["flags"])
+
+
+def test_cube_ten_steps_mixed_vs_fp64():
+    st, eos, _, _ = I.cube_state()
+    g64, _, _ = _run(st, eos, None, MAT, sph.SPH_FP64, 1e-3, 10)
+    g32, _, _ = _run(st, eos, None, MAT, sph.SPH_MIXED, 1e-3, 10)
+    _close(g32, g64, 1e-5, keys=("x", "y", "z", "vx", "vy", "vz", "u"))
+    _close(g32, g64, 1e-4, keys=("S",))
+    assert np.array_equal(g32["flags"], g64["flags"])
+
+
+@pytest.mark.parametrize("prec", [sph.SPH_FP64, sph.SPH_MIXED])
+def test_yield_and_break_flags(prec):
+    # deviatoric breaking criterion with a low breaking strain so that flags
+    # appear; yielded and broken sets must equal the oracle's
+    st, eos, _, _ = I.cube_state(n_side=10, amp=0.05)
+    st["Y0"][:] = 0.02
+    st["eps_break"][:] = 0.004
+    mat = dict(MAT, break_stress=1)
+    g, _, _ = _run(st, eos, None, mat, prec, 2e-3, 8)
+    o, _ = oracle.step(st, eos, mat, None, 2e-3, 8)
+    assert (o["flags"] & 2).sum() > 0 and (o["flags"] & 1).sum() > 0
+    assert np.array_equal(g["flags"] & 2, o["flags"] & 2)
+    assert np.array_equal(g["flags"] & 1, o["flags"] & 1)
+
+
+def test_break_zero_stress_option():
+    st, eos, _, _ = I.cube_state(n_side=8, amp=0.05)
+    st["Y0"][:] = 0.05
+    st["eps_break"][:] = 0.002
+    mat = dict(MAT, break_stress=1, break_zero_S=1)
+    g, _, _ = _run(st, eos, None, mat, sph.SPH_FP64, 2e-3, 6)
+    o, _ = oracle.step(st, eos, mat, None, 2e-3, 6)
+    assert np.array_equal(g["flags"], o["flags"])
+    _close(g, o, 1e-11, keys=("S", "mu"))
+
+
+def test_star_steps_with_metric_and_h_update():
+    st, eos, met, _ = I.star_state(6000, seed=4, amp_l0=1e-2, amp_l2=1e-2)
+    dt = I.cfl_dt(st, eos)
+    opts = dict(h_nmin=55, h_nmax=65)
+    g, _, _ = _run(st, eos, met, MAT, sph.SPH_FP64, dt, 4, opts)
+    o, _ = oracle.step(st, eos, MAT, met, dt, 4, h_nmin=55, h_nmax=65)
+    assert np.array_equal(g["h"], o["h"])
+    _close(g, o, 1e-11)
+
+
+@pytest.mark.parametrize("prec", [sph.SPH_FP64, sph.SPH_MIXED])
+def test_graph_replay_matches_direct_launches(prec):
+    st, eos = I.random_state(3000, seed=5, box=6.0, vel=0.1, stress=0.03)
+    a, _, _ = _run(st, eos, None, MAT, prec, 1e-3, 5, dict(use_graph=1))
+    b, _, _ = _run(st, eos, None, MAT, prec, 1e-3, 5, dict(use_graph=0))
+    for k in KEYS + ("flags",):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("prec", [sph.SPH_FP64, sph.SPH_MIXED])
+def test_checkpoint_resume_bit_exact(prec):
+    st, eos = I.random_state(2500, seed=6, box=6.0, vel=0.2, stress=0.05)
+    full, _, _ = _run(st, eos, None, MAT, prec, 1e-3, 6)
+    dev = sph.device_state(st)
+    ctx = _ctx(dev, eos, MAT, None, prec)
+    sph.sph_step(ctx, 1e-3, 2)
+    blob = sph.sph_get_state(ctx)
+    # resume in a fresh context bound to fresh buffers
+    st2 = {k: (None if v is None else np.zeros_like(v)) for k, v in st.items()}
+    st2["h"][:] = 1.0
+    st2["m"] = st["m"].copy()
+    st2["star"] = st["star"].copy()
+    dev2 = sph.device_state(st2)
+    ctx2 = _ctx(dev2, eos, MAT, None, prec)
+    sph.sph_set_state(ctx2, blob)
+    sph.sph_step(ctx2, 1e-3, 4)
+    sph.sph_sync(ctx2)
+    res = sph.to_numpy(dev2)
+    for k in KEYS + ("flags",):
+        assert np.array_equal(res[k], full[k]), k
+
+
+def test_totals_match_oracle():
+    st, eos, _, _ = I.cube_state(n_side=10)
+    g, ctx, _ = _run(st, eos, None, MAT, sph.SPH_FP64, 1e-3, 3)
+    o, ro = oracle.step(st, eos, MAT, None, 1e-3, 3)
+    tg = sph.sph_totals(ctx)
+    to = oracle.totals(o, ro["ncount"])
+    assert np.allclose(tg, to, rtol=1e-11, atol=1e-12 * np.abs(to).max())
+
+
+def test_energy_conservation_short_run():
+    st, eos = I.random_state(3375, seed=7, box=7.0, lattice=True, vel=0.02, stress=0.0,
+                             solid_frac=0.0)
+    st["h"][:] = 1.3 * 7.0 / 15
+    dev = sph.device_state(st)
+    ctx = _ctx(dev, eos, MAT, None, sph.SPH_MIXED)
+    e0 = sph.sph_totals(ctx)[6]
+    sph.sph_step(ctx, 2e-3, 20)
+    e1 = sph.sph_totals(ctx)[6]
+    assert abs(e1 - e0) < 1e-4 * abs(e0)
+
+
+def test_batch_equals_separate_stars():
+    # three independent stars in one index space vs each star alone
+    st, eos = I.random_state(2400, seed=8, box=5.0, nstars=3, vel=0.1, stress=0.03)
+    o_all = oracle.rhs(st, eos, MAT, None)
+    from _parity import gpu_rhs
+
+    g_all, _, _ = gpu_rhs(st, eos, MAT, None, sph.SPH_FP64)
+    for s in range(3):
+        ids = np.where(st["star"] == s)[0]
+        sub = {k: (v[..., ids] if v is not None else None) for k, v in st.items()}
+        sub["star"] = np.zeros(len(ids), np.int32)
+        e1 = dict(K=eos["K"][s:s + 1], Gamma=eos["Gamma"][s:s + 1])
+        g1, _, _ = gpu_rhs(sub, e1, MAT, None, sph.SPH_FP64)
+        for k in ("ax", "D", "dudt"):
+            assert np.allclose(g1[k], g_all[k][ids], rtol=1e-12, atol=1e-13 * np.abs(o_all[k]).max())
+        assert np.array_equal(g1["ncount"], g_all["ncount"][ids])
