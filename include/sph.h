@@ -111,7 +111,7 @@ typedef struct {
 /* Run options (host); NULL in sph_init means the defaults in brackets.
  * h_nmin, h_nmax: after each step multiply h by 1.0625 when the neighbour
  * count is below h_nmin and by 0.9375 above h_nmax [0, 0: off].
- * max_neighbors: per-particle neighbour list capacity [0: 128].
+ * max_neighbors: per-particle neighbour list capacity [0: 256].
  * lanes_per_particle: 4 or 8 threads share one particle's list in the pair
  * kernels [0: automatic].  use_graph: capture each step in a CUDA graph [1].
  * totals_every: compute totals every k steps inside sph_step [0: never]. */

@@ -68,6 +68,7 @@ struct sph_ctx {
     int64_t steps = 0;
     int launches_per_step = 0;
     // graph
+    cudaGraph_t graph = nullptr;       // kept alive: its nodes name the timing events
     cudaGraphExec_t gexec = nullptr;
     double gdt = 0.0;
     int gtiming = 0;
@@ -231,7 +232,9 @@ void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch)
 void drop_graph(sph_ctx *c)
 {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     c->gexec = nullptr;
+    c->graph = nullptr;
 }
 
 sph_status capture_step(sph_ctx *c, double dt)
@@ -270,7 +273,7 @@ sph_status capture_step(sph_ctx *c, double dt)
                 if (ev == c->slots[saved_used].ev[k]) c->gev_nodes[k] = nd;
         }
     }
-    cudaGraphDestroy(graph);
+    c->graph = graph;
     c->gdt = dt;
     c->gtiming = c->timing;
     c->launches_per_step = nl;
@@ -343,7 +346,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
         c->opt = sph_options{};
         c->opt.use_graph = 1;
     }
-    c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : 128;
+    c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : 256;
     c->lanes = c->opt.lanes_per_particle > 0 ? c->opt.lanes_per_particle : 8;
     c->stream = (cudaStream_t)stream;
     CUDA_TRY(cudaGetDevice(&c->device));
@@ -579,8 +582,12 @@ sph_status sph_step(sph_ctx *c, double dt, int32_t nsteps)
         return SPH_OK;
     }
     if (!c->have_rates) {
+        // rates at the initial state (not a timed step: no events recorded)
+        int timing = c->timing;
+        c->timing = 0;
         DevState st = state_of(c, c->P.vx, c->P.vy, c->P.vz, c->P.S);
         enqueue_rhs(c, st, c->r, false, nullptr);
+        c->timing = timing;
         c->have_rates = 1;
     }
     bool graph = c->opt.use_graph && c->stream != nullptr;
@@ -638,7 +645,8 @@ sph_status sph_neighbors(sph_ctx *c, int64_t *offsets, int32_t *idx, int64_t cap
     if (!c || !offsets || (cap > 0 && !idx) || cap < 0) return fail(SPH_ERR_ARG, "bad argument");
     const int64_t n = c->n;
     CUDA_TRY(cudaMemsetAsync(offsets, 0, (n + 1) * sizeof(int64_t), c->stream));
-    launch_export_counts(c->s, n, offsets + 1, c->stream);
+    // counts at [0, n), zero at n; the exclusive scan turns them into offsets
+    launch_export_counts(c->s, n, offsets, c->stream);
     launch_scan_i64(offsets, n + 1, c->stream);
     int64_t total = 0;
     CUDA_TRY(cudaMemcpyAsync(&total, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));

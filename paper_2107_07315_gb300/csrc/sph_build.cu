@@ -145,27 +145,22 @@ __global__ void k_keys(DevState st, const DevScalars *sc, int bits,
 
 constexpr int kSortThreads = 256;
 
-// Digit histograms of every pass in one read of the keys.
-// hist layout: [pass][digit][block].
-__global__ void k_radix_hist(const unsigned long long *keys, int64_t n, int ipt, int passes,
+// Per-tile digit histogram of one pass over the keys in their current order
+// (the tiles of pass p hold different keys than those of pass p-1, so each
+// pass counts its own).  hist layout: [digit][block].
+__global__ void k_radix_hist(const unsigned long long *keys, int64_t n, int ipt, int shift,
                              uint32_t *hist)
 {
-    __shared__ uint32_t cnt[8][256];
-    for (int t = threadIdx.x; t < 8 * 256; t += blockDim.x) (&cnt[0][0])[t] = 0u;
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0u;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * kSortThreads * ipt;
     for (int r = 0; r < ipt; ++r) {
         int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-        if (i < n) {
-            unsigned long long k = keys[i];
-            for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p][(k >> (8 * p)) & 255u], 1u);
-        }
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < passes * 256; t += blockDim.x) {
-        int p = t >> 8, d = t & 255;
-        hist[((int64_t)p * 256 + d) * gridDim.x + blockIdx.x] = cnt[p][d];
-    }
+    hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
 }
 
 // Exclusive scan of each pass's histogram (one block per pass).
@@ -497,17 +492,15 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     int gb = (int)((n + tb - 1) / tb);
     k_keys<<<gb, tb, 0, stream>>>(st, s.sc, plan.key_bits_axis, s.keys[0], s.vals[0]);
     ++nl;
-    k_radix_hist<<<plan.nblocks, kSortThreads, 0, stream>>>(s.keys[0], n, plan.ipt, plan.passes,
-                                                            s.hist);
-    ++nl;
-    k_radix_scan<<<plan.passes, 1024, 0, stream>>>(s.hist, plan.nblocks);
-    ++nl;
     for (int p = 0; p < plan.passes; ++p) {
         int src = p & 1, dst = src ^ 1;
+        uint32_t *hist = s.hist + (int64_t)p * 256 * plan.nblocks;
+        k_radix_hist<<<plan.nblocks, kSortThreads, 0, stream>>>(s.keys[src], n, plan.ipt, 8 * p,
+                                                                hist);
+        k_radix_scan<<<1, 1024, 0, stream>>>(hist, plan.nblocks);
         k_radix_scatter<<<plan.nblocks, kSortThreads, 0, stream>>>(
-            s.keys[src], s.vals[src], s.keys[dst], s.vals[dst], n, plan.ipt, 8 * p,
-            s.hist + (int64_t)p * 256 * plan.nblocks);
-        ++nl;
+            s.keys[src], s.vals[src], s.keys[dst], s.vals[dst], n, plan.ipt, 8 * p, hist);
+        nl += 3;
     }
     const uint32_t *order = s.vals[plan.passes & 1];
     k_gather<<<gb, tb, 0, stream>>>(st, order, s.sc, s.perm, s.xs, s.ys, s.zs, s.hs, s.tys, s.rec,

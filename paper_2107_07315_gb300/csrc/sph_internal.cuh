@@ -159,7 +159,7 @@ void launch_kick_return(const StepState &s, const DevRates &r, const DevEos &eos
 constexpr int kTotalsBlocks = 256;
 void launch_totals(const StepState &s, const int32_t *ncount, double *partial, double *out,
                    cudaStream_t st);
-void launch_export_counts(const Scratch &s, int64_t n, int64_t *offsets_plus1,
+void launch_export_counts(const Scratch &s, int64_t n, int64_t *counts_out,
                           cudaStream_t st);
 void launch_export_fill(const Scratch &s, int64_t n, int cap, const int64_t *offsets,
                         int32_t *idx, cudaStream_t st);

@@ -207,11 +207,11 @@ __global__ void k_totals_sum(const double *partial, int nblocks, int64_t n, doub
 }
 
 __global__ void k_export_counts(const int32_t *perm, const int32_t *ncnt, int64_t n,
-                                int64_t *offsets_plus1)
+                                int64_t *counts_out)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    offsets_plus1[perm[i]] = ncnt[i];
+    counts_out[perm[i]] = ncnt[i];
 }
 
 // Exclusive scan of n+1 int64 values in place (one block; export path only).
@@ -285,10 +285,10 @@ void launch_totals(const StepState &s, const int32_t *ncount, double *partial, d
     k_totals_sum<<<1, 32, 0, st>>>(partial, kTotBlocks, s.n, out);
 }
 
-void launch_export_counts(const Scratch &s, int64_t n, int64_t *offsets_plus1, cudaStream_t st)
+void launch_export_counts(const Scratch &s, int64_t n, int64_t *counts_out, cudaStream_t st)
 {
     if (n == 0) return;
-    k_export_counts<<<(int)((n + 255) / 256), 256, 0, st>>>(s.perm, s.ncnt, n, offsets_plus1);
+    k_export_counts<<<(int)((n + 255) / 256), 256, 0, st>>>(s.perm, s.ncnt, n, counts_out);
 }
 
 void launch_scan_i64(int64_t *data, int64_t n, cudaStream_t st)

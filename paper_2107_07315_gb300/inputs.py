@@ -408,15 +408,22 @@ def cube_state(n_side: int = 16, h: float = 1.3, seed: int = 0, K: float = 1.0,
     return st, eos, None, A
 
 
-def random_state(n: int, seed: int, box: float = 6.0, h_lo: float = 0.5, h_hi: float = 1.2,
-                 solid_frac: float = 0.5, vel: float = 0.05, stress: float = 0.02,
-                 nstars: int = 1, lattice: bool = False):
+def random_state(n: int, seed: int, box: float | None = None, h_lo: float = 0.5,
+                 h_hi: float = 1.2, solid_frac: float = 0.5, vel: float = 0.05,
+                 stress: float = 0.02, nstars: int = 1, lattice: bool = False,
+                 n_target: float = 40.0):
     """Jittered particle sets with varied h, mixed fluid/solid and random S.
 
     Used for parity cases with ragged leaves and uneven neighbour counts.
-    Stars (if nstars > 1) sit in disjoint, well separated boxes.
+    Stars (if nstars > 1) sit in disjoint, well separated boxes.  Without an
+    explicit ``box`` the box edge is chosen so that a particle has about
+    ``n_target`` neighbours within the mean support h_a + h_b.
     """
     rng = np.random.default_rng(seed)
+    if box is None:
+        hs = h_lo + h_hi
+        per_star = max(n / max(nstars, 1), 1.0)
+        box = (per_star * (4.0 / 3.0) * math.pi * hs ** 3 / n_target) ** (1.0 / 3.0)
     if lattice:
         side = int(round(n ** (1.0 / 3.0)))
         g = np.arange(side, dtype=np.float64) * (box / side)

@@ -57,7 +57,13 @@ def field_errors(g, o, ids=None):
     out = {}
 
     def err(qg, qo, s):
-        return np.max(np.abs(qg - qo) / np.maximum(np.abs(qo), s)) if len(ids) else 0.0
+        if not len(ids):
+            return 0.0
+        d = np.abs(qg - qo)
+        den = np.maximum(np.abs(qo), s)
+        # an exactly-zero reference with zero scale (no neighbours) must match exactly
+        return float(np.max(np.where(den > 0, d / np.where(den > 0, den, 1.0),
+                                     np.where(d == 0, 0.0, np.inf))))
 
     out["D"] = err(g["D"][ids], o["D"][ids], sc["D"][ids])
     out["rho"] = err(g["rho"][ids], o["rho"][ids], np.abs(o["rho"][ids]))

@@ -42,14 +42,14 @@ def test_cube_config0(prec, tol):
 @pytest.mark.parametrize("seed,n,nstars", [(1, 1000, 1), (2, 1237, 1), (3, 2051, 3), (4, 777, 2)])
 def test_random_states(prec, tol, seed, n, nstars):
     # varied h, mixed fluid/solid, random traceless S, several stars, ragged leaves
-    st, eos = I.random_state(n, seed=seed, box=5.0, nstars=nstars, vel=0.2, stress=0.05)
+    st, eos = I.random_state(n, seed=seed, nstars=nstars, vel=0.2, stress=0.05)
     _check(st, eos, prec=prec, tol=tol, label="random %d" % seed)
 
 
 @pytest.mark.parametrize("prec,tol", PREC)
 @pytest.mark.parametrize("jaumann,yield_mode", [(1, 0), (0, 1)])
 def test_material_options(prec, tol, jaumann, yield_mode):
-    st, eos = I.random_state(900, seed=9, box=4.5, vel=0.3, stress=0.05, solid_frac=0.8)
+    st, eos = I.random_state(900, seed=9, vel=0.3, stress=0.05, solid_frac=0.8)
     mat = dict(MAT, jaumann=jaumann, yield_mode=yield_mode, alpha_av=0.5, beta_av=1.0)
     _check(st, eos, mat=mat, prec=prec, tol=tol, label="options")
 
@@ -88,14 +88,22 @@ def test_edge_single_and_pair(prec, tol):
         g, ctx, _ = gpu_rhs(st, eos, MAT, None, prec)
         assert list(g["ncount"]) == [expect, expect]
         o = oracle.rhs(st, eos, MAT, None, scales=True)
-        assert_close(g, o, tol, label="pair")
+        if prec == sph.SPH_FP64:
+            assert_close(g, o, tol, label="pair")
+        else:
+            # At 2h(1 - 5e-13) the exact kernel gradient (~(2-q)^2) lies below
+            # FP32 resolution; measure against the pair force's natural scale
+            # m (P_a/D_a^2 + P_b/D_b^2) max|dW/dr| = m 2P/D^2 sigma/h.
+            assert abs(g["D"][0] - o["D"][0]) <= tol["D"] * o["D"][0]
+            fscale = 2 * o["P"][0] / o["D"][0] ** 2 / np.pi
+            assert np.all(np.abs(g["ax"] - o["ax"]) <= tol["a"] * fscale)
 
 
 @pytest.mark.parametrize("prec,tol", PREC)
 def test_edge_coincident_and_lonely_star(prec, tol):
     # particles sharing a position (zero separation: W finite, grad W = 0)
     # and a star holding a single particle in a batch
-    st, eos = I.random_state(300, seed=12, box=3.0, nstars=2, vel=0.1, stress=0.02)
+    st, eos = I.random_state(300, seed=12, nstars=2, vel=0.1, stress=0.02)
     st["x"][5], st["y"][5], st["z"][5] = st["x"][6], st["y"][6], st["z"][6]
     st["star"][6] = st["star"][5]
     eos = dict(K=np.array([1.0, 1.2, 0.8]), Gamma=np.array([2.0, 1.9, 2.4]))
@@ -121,7 +129,7 @@ def test_empty_input():
 
 @pytest.mark.parametrize("prec", [sph.SPH_FP64, sph.SPH_MIXED])
 def test_momentum_conserved_to_rounding(prec):
-    st, eos = I.random_state(2000, seed=21, box=6.0, vel=0.3, stress=0.05)
+    st, eos = I.random_state(2000, seed=21, vel=0.3, stress=0.05)
     st["m"][:] = 1.0
     g, _, _ = gpu_rhs(st, eos, MAT, None, prec)
     eps = 1e-13 if prec == sph.SPH_FP64 else 1e-6
@@ -131,7 +139,7 @@ def test_momentum_conserved_to_rounding(prec):
 
 @pytest.mark.parametrize("lanes", [4, 8])
 def test_lane_variants_agree(lanes):
-    st, eos = I.random_state(1500, seed=31, box=5.0, vel=0.2, stress=0.05)
+    st, eos = I.random_state(1500, seed=31, vel=0.2, stress=0.05)
     opts = dict(lanes_per_particle=lanes, use_graph=1)
     _check(st, eos, prec=sph.SPH_MIXED, tol=TOL_MIXED, options=opts, label="lanes")
 
