@@ -190,6 +190,26 @@ sph_status sph_set_state(sph_ctx *ctx, const void *host_buf, int64_t bytes);
 /* Release the context and its device memory (the caller's buffers stay). */
 void sph_free(sph_ctx *ctx);
 
+/* Neighbour lists without a context and without any device allocation, for
+ * callers that cannot call cudaMalloc: plug-ins whose host application owns
+ * all device memory through its own pool, processes whose memory budget
+ * forbids further allocations, and time-critical loops where an allocator
+ * call (which may synchronise the device) is not allowed.  The paper has no
+ * counterpart; this is a library service.  Same lists and CSR layout as
+ * sph_neighbors for one star: x, y, z, h are device arrays of n particles
+ * (caller order), offsets a device int64[n+1], idx a device int32[cap];
+ * cuda_stream a cudaStream_t (NULL: legacy default stream).  Scratch is one
+ * fixed device array of about 10.6 MB inside the library, present on every
+ * GPU that loads it until the process exits; limits: n <= 16384 (larger n
+ * returns SPH_ERR_ARG) and at most 128 neighbours per particle
+ * (SPH_ERR_CAPACITY).  The first call on a device looks up the array's
+ * device address (make that call before any stream capture).  Every call
+ * shares the array and resets what must start at zero; calls that overlap on
+ * the GPU race.  Synchronous. */
+sph_status sph_neighbors_noalloc(int64_t n, const double *x, const double *y, const double *z,
+                                 const double *h, int64_t *offsets, int32_t *idx, int64_t cap,
+                                 void *cuda_stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char *sph_last_error(void);
 

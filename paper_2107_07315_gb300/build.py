@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sph_build.cu", "sph_pairs.cu", "sph_step.cu", "sph_api.cu"]
+SOURCES = ["sph_build.cu", "sph_pairs.cu", "sph_step.cu", "sph_api.cu", "sph_noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -816,3 +816,5 @@ void sph_free(sph_ctx *c)
 const char *sph_last_error(void) { return g_err; }
 
 }  // extern "C"
+
+void sph::record_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }

@@ -165,4 +165,7 @@ void launch_export_fill(const Scratch &s, int64_t n, int cap, const int64_t *off
                         int32_t *idx, cudaStream_t st);
 void launch_scan_i64(int64_t *data, int64_t n, cudaStream_t st);
 
+// Store a message for sph_last_error() on the calling thread (sph_api.cu).
+void record_error(const char *msg);
+
 }  // namespace sph

@@ -26,7 +26,7 @@ STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
 # Every symbol include/sph.h declares.
 EXPORTS = ("sph_init", "sph_rhs", "sph_step", "sph_sync", "sph_neighbors", "sph_totals",
            "sph_stats", "sph_timing", "sph_timing_read", "sph_state_size", "sph_get_state",
-           "sph_set_state", "sph_free", "sph_last_error")
+           "sph_set_state", "sph_free", "sph_last_error", "sph_neighbors_noalloc")
 
 
 class SphError(RuntimeError):
@@ -101,6 +101,7 @@ def lib():
         L.sph_set_state.argtypes = [vp, vp, C.c_int64]
         L.sph_free.argtypes = [vp]
         L.sph_free.restype = None
+        L.sph_neighbors_noalloc.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, C.c_int64, vp]
         L.sph_last_error.restype = C.c_char_p
         for f in EXPORTS:
             if f not in ("sph_free", "sph_last_error"):
@@ -281,6 +282,15 @@ def sph_set_state(ctx: SphCtx, buf: np.ndarray) -> None:
     buf = np.ascontiguousarray(buf, dtype=np.uint8)
     _check(lib().sph_set_state(ctx.handle, buf.ctypes.data_as(C.c_void_p), len(buf)),
            "sph_set_state")
+
+
+def sph_neighbors_noalloc(n: int, x, y, z, h, offsets, idx, cap: int, stream=None) -> None:
+    """Neighbour CSR of one star with no context and no device allocation
+    (for callers that cannot call cudaMalloc); n <= 16384."""
+    _check(lib().sph_neighbors_noalloc(int(n), _ptr(x), _ptr(y), _ptr(z), _ptr(h),
+                                       _ptr(offsets), _ptr(idx), int(cap),
+                                       C.c_void_p(stream) if stream else None),
+           "sph_neighbors_noalloc")
 
 
 def sph_free(ctx: SphCtx) -> None:
