@@ -383,20 +383,9 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     }
     c->nleaves = (int)leaf_star.size();
     // Tree levels.
-    c->tl.nlevels = 0;
     int64_t total_nodes = 0;
-    if (c->nleaves > 0) {
-        int cnt = c->nleaves;
-        while (true) {
-            if (c->tl.nlevels >= kMaxLevels) return fail(SPH_ERR_ARG, "too many tree levels");
-            c->tl.count[c->tl.nlevels] = cnt;
-            c->tl.offset[c->tl.nlevels] = (int)total_nodes;
-            total_nodes += cnt;
-            c->tl.nlevels++;
-            if (cnt == 1) break;
-            cnt = (cnt + 1) / 2;
-        }
-    }
+    if (!make_tree_levels(c->nleaves, c->tl, &total_nodes) || c->tl.nlevels > 10)
+        return fail(SPH_ERR_ARG, "too many particles for the tree (more than 10 levels)");
     // Sort plan.
     int sb = 0;
     while ((1 << sb) < c->nstars) ++sb;
@@ -418,12 +407,14 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     STATUS_TRY(c->alloc(&s.vals[0], nn));
     STATUS_TRY(c->alloc(&s.vals[1], nn));
     STATUS_TRY(c->alloc(&s.hist, (size_t)c->plan.passes * 256 * c->plan.nblocks));
+    STATUS_TRY(c->alloc(&s.radix_tot, (size_t)8 * 256));
     STATUS_TRY(c->alloc(&s.xs, nn));
     STATUS_TRY(c->alloc(&s.ys, nn));
     STATUS_TRY(c->alloc(&s.zs, nn));
     STATUS_TRY(c->alloc(&s.hs, nn));
     STATUS_TRY(c->alloc(&s.tys, nn));
     STATUS_TRY(c->alloc(&s.rec, 4 * nn));
+    STATUS_TRY(c->alloc(&s.pos4, nn));
     STATUS_TRY(c->alloc(&s.sd2, 2 * nn));
     STATUS_TRY(c->alloc(&s.pp, 2 * nn));
     if (prec == SPH_FP64) {

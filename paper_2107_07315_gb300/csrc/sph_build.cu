@@ -80,12 +80,29 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
     }
     __syncthreads();
     if (!last) return;
-    if (threadIdx.x < 3) {
-        int k = threadIdx.x;
+    // all threads of the last block reduce the block partials
+    for (int k = 0; k < 3; ++k) {
         double a = 1e300, b = -1e300;
-        for (int w = 0; w < (int)gridDim.x; ++w) {
+        for (int w = threadIdx.x; w < (int)gridDim.x; w += blockDim.x) {
             a = fmin(a, __ldcg(&partial[w * 6 + k]));
             b = fmax(b, __ldcg(&partial[w * 6 + 3 + k]));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_lo[k][threadIdx.x >> 5] = a;
+            s_hi[k][threadIdx.x >> 5] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int k = threadIdx.x;
+        double a = s_lo[k][0], b = s_hi[k][0];
+        for (int w = 1; w < kBoxThreads / 32; ++w) {
+            a = fmin(a, s_lo[k][w]);
+            b = fmax(b, s_hi[k][w]);
         }
         sc->bbox_lo[k] = enc_double(a);
         sc->bbox_hi[k] = enc_double(b);
@@ -101,7 +118,13 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
         int e = 0;
         frexp(fmax(m, 1e-300), &e);  // m < 2^e
         sc->grid = ldexp(1.0, e - 22);
+        sc->grid_inv = ldexp(1.0, 22 - e);
+        for (int k = 0; k < 3; ++k) {
+            double ext = dec_double(sc->bbox_hi[k]) - dec_double(sc->bbox_lo[k]);
+            sc->inv_ext[k] = ext > 0.0 ? 1.0 / ext : 0.0;
+        }
         sc->eps_abs = 1e-6 * fmax(m, 1e-30);
+        sc->screen_c1 = (float)(1.67e-6 * m);
         sc->pairs_last = 0ull;
         sc->tree_done = 0;
         sc->rhs_count += 1ull;
@@ -131,7 +154,7 @@ __global__ void k_keys(DevState st, const DevScalars *sc, int bits,
     for (int k = 0; k < 3; ++k) {
         double lo = dec_double(sc->bbox_lo[k]), hi = dec_double(sc->bbox_hi[k]);
         double ext = hi - lo;
-        double t = ext > 0.0 ? (p[k] - lo) / ext * cells : 0.0;
+        double t = ext > 0.0 ? (p[k] - lo) * sc->inv_ext[k] * cells : 0.0;
         t = fmin(fmax(t, 0.0), cells - 1.0);
         q[k] = (uint32_t)t;
     }
@@ -149,7 +172,7 @@ constexpr int kSortThreads = 256;
 // (the tiles of pass p hold different keys than those of pass p-1, so each
 // pass counts its own).  hist layout: [digit][block].
 __global__ void k_radix_hist(const unsigned long long *keys, int64_t n, int ipt, int shift,
-                             uint32_t *hist)
+                             uint32_t *hist, uint32_t *digit_total)
 {
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0u;
@@ -160,40 +183,44 @@ __global__ void k_radix_hist(const unsigned long long *keys, int64_t n, int ipt,
         if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
+    uint32_t c = cnt[threadIdx.x];
+    hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = c;
+    if (c) atomicAdd(&digit_total[threadIdx.x], c);
 }
 
-// Exclusive scan of each pass's histogram (one block per pass).
-__global__ void k_radix_scan(uint32_t *hist, int nblocks)
+// Exclusive offsets of one pass: block d handles digit d.  Its base is the
+// number of keys with a smaller digit (sum of the digit totals below d); the
+// row of per-tile counts is then scanned in tile order.
+__global__ void k_radix_scan(uint32_t *hist, const uint32_t *digit_total, int nblocks)
 {
-    const int T = 1024;
-    __shared__ uint32_t wsum[32];
-    uint32_t *h = hist + (int64_t)blockIdx.x * 256 * nblocks;
-    int64_t total = (int64_t)256 * nblocks;
-    int64_t chunk = (total + T - 1) / T;
-    int64_t b0 = threadIdx.x * chunk, b1 = min(b0 + chunk, total);
+    __shared__ uint32_t wsum[8];
+    const int d = blockIdx.x, t = threadIdx.x;
+    const int lane = t & 31, w = t >> 5;
+    // base = sum of totals of digits < d
+    uint32_t v = t < d ? digit_total[t] : 0u;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[w] = v;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int k = 0; k < 8; ++k) base += wsum[k];
+    __syncthreads();
+    // scan of the row hist[d][0 .. nblocks)
+    uint32_t *h = hist + (int64_t)d * nblocks;
+    int chunk = (nblocks + 255) / 256;
+    int b0 = t * chunk, b1 = min(b0 + chunk, nblocks);
     uint32_t s = 0;
-    for (int64_t i = b0; i < b1; ++i) s += h[i];
-    // block exclusive scan of s
-    uint32_t v = s;
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = b0; i < b1; ++i) s += h[i];
+    uint32_t x = s;
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    if (lane == 31) wsum[w] = v;
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
-    if (w == 0) {
-        uint32_t x = wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += t;
-        }
-        wsum[lane] = x;
-    }
-    __syncthreads();
-    uint32_t run = v - s + (w > 0 ? wsum[w - 1] : 0u);
-    for (int64_t i = b0; i < b1; ++i) {
+    uint32_t woff = 0;
+    for (int k = 0; k < w; ++k) woff += wsum[k];
+    uint32_t run = base + woff + x - s;
+    for (int i = b0; i < b1; ++i) {
         uint32_t c = h[i];
         h[i] = run;
         run += c;
@@ -247,7 +274,7 @@ __global__ void k_radix_scatter(const unsigned long long *kin, const uint32_t *v
 // Sorted copies and the FP32 j-record halves read by the list build.
 __global__ void k_gather(DevState st, const uint32_t *order, const DevScalars *sc, int32_t *perm,
                          double *xs, double *ys, double *zs, double *hs, uint8_t *tys,
-                         float4 *rec, double4_32a *rec64)
+                         float4 *rec, float4 *pos4, double4_32a *rec64)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= st.n) return;
@@ -263,12 +290,13 @@ __global__ void k_gather(DevState st, const uint32_t *order, const DevScalars *s
     double g = sc->grid;
     float hi[3], lo[3];
     for (int k = 0; k < 3; ++k) {
-        double H = g * rint(p[k] / g);
+        double H = g * rint(p[k] * sc->grid_inv);  // grid is a power of two: exact
         hi[k] = (float)H;
         lo[k] = (float)(p[k] - H);
     }
     rec[i * 4 + 0] = make_float4(hi[0], hi[1], hi[2], (float)h);
     rec[i * 4 + 1] = make_float4(lo[0], lo[1], lo[2], (float)m);
+    pos4[i] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)h);
     if (rec64) {
         rec64[i * 3 + 0] = make_double4_32a(p[0], p[1], p[2], h);
         rec64[i * 3 + 1].x = m;
@@ -288,7 +316,7 @@ __device__ __forceinline__ float4 node_merge_b(float4 a, float4 b)
                        __int_as_float(lo | (hi << 16)));
 }
 
-// Leaf boxes and the implicit binary tree above them.  Boxes are rounded
+// Leaf boxes and the implicit 8-ary tree above them.  Boxes are rounded
 // outward to FP32 so that they contain every FP64 position of the node.
 __global__ void k_tree(const double *xs, const double *ys, const double *zs, const double *hs,
                        const int32_t *leaf_start, const int32_t *leaf_star, TreeLevels tl,
@@ -320,29 +348,32 @@ __global__ void k_tree(const double *xs, const double *ys, const double *zs, con
     sa[t] = a;
     sb[t] = b;
     __syncthreads();
+    // In-block levels: node k of level v+1 is the union of nodes 8k..8k+7 of
+    // level v.  A block of 512 leaves holds three such levels.
     int top_local = min(tl.nlevels - 1, kTreeBlockLevels);
-    for (int k = 1; k <= top_local; ++k) {
-        int width = kTreeBlock >> k;
+    for (int v = 1; v <= top_local; ++v) {
+        int width = kTreeBlock >> (3 * v);
         int node = blockIdx.x * width + t;
         float4 na, nb;
         bool act = t < width;
         if (act) {
-            int cl = 2 * t, cr = 2 * t + 1;
-            int gl = blockIdx.x * (kTreeBlock >> (k - 1)) + cr;
-            na = sa[cl];
-            nb = sb[cl];
-            if (gl < tl.count[k - 1]) {
-                na = node_merge_a(na, sa[cr]);
-                nb = node_merge_b(nb, sb[cr]);
+            int child0 = blockIdx.x * (kTreeBlock >> (3 * (v - 1))) + 8 * t;
+            na = sa[8 * t];
+            nb = sb[8 * t];
+            for (int c = 1; c < kBranch; ++c) {
+                if (child0 + c < tl.count[v - 1]) {
+                    na = node_merge_a(na, sa[8 * t + c]);
+                    nb = node_merge_b(nb, sb[8 * t + c]);
+                }
             }
         }
         __syncthreads();
         if (act) {
             sa[t] = na;
             sb[t] = nb;
-            if (node < tl.count[k]) {
-                nodes[2 * ((int64_t)tl.offset[k] + node) + 0] = na;
-                nodes[2 * ((int64_t)tl.offset[k] + node) + 1] = nb;
+            if (node < tl.count[v]) {
+                nodes[2 * ((int64_t)tl.offset[v] + node) + 0] = na;
+                nodes[2 * ((int64_t)tl.offset[v] + node) + 1] = nb;
             }
         }
         __syncthreads();
@@ -356,16 +387,18 @@ __global__ void k_tree(const double *xs, const double *ys, const double *zs, con
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int k = kTreeBlockLevels + 1; k < tl.nlevels; ++k) {
-        for (int node = t; node < tl.count[k]; node += kTreeBlock) {
-            int64_t c = (int64_t)tl.offset[k - 1] + 2 * node;
+    for (int v = kTreeBlockLevels + 1; v < tl.nlevels; ++v) {
+        for (int node = t; node < tl.count[v]; node += kTreeBlock) {
+            int64_t c = (int64_t)tl.offset[v - 1] + (int64_t)kBranch * node;
             float4 na = __ldcg(&nodes[2 * c]), nb = __ldcg(&nodes[2 * c + 1]);
-            if (2 * node + 1 < tl.count[k - 1]) {
-                na = node_merge_a(na, __ldcg(&nodes[2 * (c + 1)]));
-                nb = node_merge_b(nb, __ldcg(&nodes[2 * (c + 1) + 1]));
+            for (int k = 1; k < kBranch; ++k) {
+                if ((int64_t)kBranch * node + k < tl.count[v - 1]) {
+                    na = node_merge_a(na, __ldcg(&nodes[2 * (c + k)]));
+                    nb = node_merge_b(nb, __ldcg(&nodes[2 * (c + k) + 1]));
+                }
             }
-            nodes[2 * ((int64_t)tl.offset[k] + node) + 0] = na;
-            nodes[2 * ((int64_t)tl.offset[k] + node) + 1] = nb;
+            nodes[2 * ((int64_t)tl.offset[v] + node) + 0] = na;
+            nodes[2 * ((int64_t)tl.offset[v] + node) + 1] = nb;
         }
         __threadfence_block();
         __syncthreads();
@@ -383,90 +416,159 @@ __device__ __forceinline__ bool pair_in_fp64(double xa, double ya, double za, do
     return r2 < __dmul_rn(hsum, hsum);
 }
 
-constexpr int kListThreads = 128;
+constexpr int kListThreads = 64;
+constexpr int kListWarps = kListThreads / 32;
+constexpr int kCandCap = 160;                          // candidate leaves buffered per warp
+constexpr int kStackCap = (kBranch - 1) * 10 + 2;      // depth bound for <= 10 levels
 
-// One thread per sorted particle: depth-first walk of the tree (left child
-// first, so neighbours come out in ascending sorted index), pruning nodes
-// whose box lies farther than h_i + h_max(node) from the particle, then the
-// screened predicate on the particles of each surviving leaf.
+// One warp per 32 consecutive sorted particles.  Phase 1 walks the implicit
+// 8-ary tree depth first with a warp-uniform stack: the 8 children of a node
+// are tested together (one ballot each: bit l set when the child box lies
+// within h_l + h_max(child) of lane l's particle), surviving inner children
+// are pushed in reverse order, surviving leaves are buffered in shared
+// memory with their ballot.  Phase 2: every lane screens the particles of the
+// buffered leaves whose ballot has its bit, in buffer order (ascending leaf,
+// hence ascending sorted index).
+//
+// Screening uses FP32 positions (pos4 = fl32(x, y, z, h)).  With u = 2^-24
+// and X = max |x|, |fl32 error of r^2 - (h_a+h_b)^2| <= 4 sqrt(3) u X r +
+// 5 u r^2 + 7 u hs^2 for r <= 2 hs; the band M = c1 hs + 3.2e-6 hs^2 with
+// c1 = 1.67e-6 X is twice that bound.  Inside the band the pair is decided
+// by the FP64 predicate.
+template <bool MULTI_STAR>
 __global__ void __launch_bounds__(kListThreads)
-k_neighbors(int64_t n, const float4 *rec, const double *xs, const double *ys, const double *zs,
+k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, const double *zs,
             const double *hs, const int32_t *leaf_start, const int32_t *leaf_star,
             const int32_t *leaf_of, TreeLevels tl, const float4 *nodes, int cap, int32_t *nbr,
             int32_t *ncnt, DevScalars *sc)
-// Stack entries pack (level << 26 | node index) in an unsigned int.
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool valid = i < n;
+    __shared__ int s_leaf[kListWarps][kCandCap];
+    __shared__ unsigned s_mask[kListWarps][kCandCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = i < n;
     int cnt = 0;
     unsigned long long nre = 0;
     bool over = false;
+    // invalid lanes sit far away: every box and pair test fails for them
+    float4 p = make_float4(3e38f, 3e38f, 3e38f, 0.f);
+    int star = 0;
     if (valid) {
-        float4 r0 = rec[i * 4 + 0], r1 = rec[i * 4 + 1];
-        const float grid = (float)sc->grid;
-        const float eps = (float)sc->eps_abs;
-        const float xi = r0.x + r1.x, yi = r0.y + r1.y, zi = r0.z + r1.z;
-        const float hi = r0.w;
-        const int star = leaf_star[leaf_of[i]];
-        unsigned stack[kMaxLevels + 2];
-        int sp = 0;
-        stack[sp++] = ((unsigned)(tl.nlevels - 1) << 26) | 0u;
-        int32_t *out = nbr + i * (int64_t)cap;
-        while (sp > 0) {
+        p = pos4[i];
+        if (MULTI_STAR) star = leaf_star[leaf_of[i]];
+    }
+    const float c1 = sc->screen_c1;
+    const float eps = (float)sc->eps_abs;
+    int32_t *out = nbr + i * (int64_t)cap;
+
+    auto box_hit = [&](const float4 &a, const float4 &b) -> bool {
+        float gx = fmaxf(fmaxf(a.x - p.x, p.x - b.x), 0.f);
+        float gy = fmaxf(fmaxf(a.y - p.y, p.y - b.y), 0.f);
+        float gz = fmaxf(fmaxf(a.z - p.z, p.z - b.z), 0.f);
+        float R = fmaf(p.w + a.w, 1.0001f, eps);
+        bool h = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+        if (MULTI_STAR) {
+            int sr = __float_as_int(b.w);
+            h = h && star >= (sr & 0xffff) && star <= (sr >> 16);
+        }
+        return h;
+    };
+
+    unsigned stack[kStackCap];
+    int sp = 0;
+    int ncand = 0;
+    const int top = tl.nlevels - 1;
+    if (top == 0) {
+        int64_t gi = tl.offset[0];
+        unsigned m = __ballot_sync(0xffffffffu, box_hit(nodes[2 * gi], nodes[2 * gi + 1]));
+        if (m) {
+            if (lane == 0) {
+                s_leaf[warp][0] = 0;
+                s_mask[warp][0] = m;
+            }
+            ncand = 1;
+        }
+    } else {
+        stack[sp++] = ((unsigned)top << 26) | 0u;
+    }
+    while (true) {
+        while (sp > 0 && ncand <= kCandCap - kBranch) {
             unsigned e = stack[--sp];
             int lv = (int)(e >> 26), k = (int)(e & ((1u << 26) - 1u));
-            int64_t gi = (int64_t)tl.offset[lv] + k;
-            float4 a = nodes[2 * gi], b = nodes[2 * gi + 1];
-            int sr = __float_as_int(b.w);
-            if (star < (sr & 0xffff) || star > (sr >> 16)) continue;
-            float gx = fmaxf(fmaxf(a.x - xi, xi - b.x), 0.f);
-            float gy = fmaxf(fmaxf(a.y - yi, yi - b.y), 0.f);
-            float gz = fmaxf(fmaxf(a.z - zi, zi - b.z), 0.f);
-            float R = fmaf(hi + a.w, 1.0001f, eps);
-            if (gx * gx + gy * gy + gz * gz >= R * R) continue;
-            if (lv > 0) {
-                int cr = 2 * k + 1;
-                if (cr < tl.count[lv - 1]) stack[sp++] = ((unsigned)(lv - 1) << 26) | (unsigned)cr;
-                stack[sp++] = ((unsigned)(lv - 1) << 26) | (unsigned)(2 * k);
-                continue;
+            int c0 = kBranch * k;
+            int nc = min(kBranch, tl.count[lv - 1] - c0);
+            int64_t base = (int64_t)tl.offset[lv - 1] + c0;
+            unsigned hm[kBranch];
+#pragma unroll
+            for (int c = 0; c < kBranch; ++c) {
+                int cc = c < nc ? c : 0;
+                float4 a = nodes[2 * (base + cc)], b = nodes[2 * (base + cc) + 1];
+                hm[c] = __ballot_sync(0xffffffffu, c < nc && box_hit(a, b));
             }
-            int j0 = leaf_start[k], j1 = leaf_start[k + 1];
-            for (int j = j0; j < j1; ++j) {
-                if (j == (int)i) continue;
-                float4 q0 = rec[(int64_t)j * 4 + 0], q1 = rec[(int64_t)j * 4 + 1];
-                float dx = (r0.x - q0.x) + (r1.x - q1.x);
-                float dy = (r0.y - q0.y) + (r1.y - q1.y);
-                float dz = (r0.z - q0.z) + (r1.z - q1.z);
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float hsum = hi + q0.w;
-                float hs2 = hsum * hsum;
-                float d = r2 - hs2;
-                float M = fmaf(4e-6f, hs2, 2e-6f * grid * hsum);
-                bool in;
-                if (d < -M) {
-                    in = true;
-                } else if (d > M) {
-                    in = false;
-                } else {
-                    ++nre;
-                    in = pair_in_fp64(xs[i], ys[i], zs[i], hs[i], xs[j], ys[j], zs[j], hs[j]);
+            if (lv == 1) {
+#pragma unroll
+                for (int c = 0; c < kBranch; ++c) {
+                    if (hm[c]) {
+                        if (lane == 0) {
+                            s_leaf[warp][ncand] = c0 + c;
+                            s_mask[warp][ncand] = hm[c];
+                        }
+                        ++ncand;
+                    }
                 }
-                if (in) {
-                    if (cnt < cap) out[cnt] = j;
-                    else over = true;
-                    ++cnt;
+            } else {
+#pragma unroll
+                for (int c = kBranch - 1; c >= 0; --c)
+                    if (hm[c]) stack[sp++] = ((unsigned)(lv - 1) << 26) | (unsigned)(c0 + c);
+            }
+        }
+        __syncwarp();
+        int cpos = 0;
+        while (true) {
+            while (cpos < ncand && !((s_mask[warp][cpos] >> lane) & 1u)) ++cpos;
+            bool have = cpos < ncand;
+            if (!__any_sync(0xffffffffu, have)) break;
+            if (have) {
+                int leaf = s_leaf[warp][cpos];
+                ++cpos;
+                int j0 = leaf_start[leaf], j1 = leaf_start[leaf + 1];
+                float4 q[kLeaf];
+#pragma unroll
+                for (int t = 0; t < kLeaf; ++t) q[t] = pos4[j0 + t < j1 ? j0 + t : j0];
+#pragma unroll
+                for (int t = 0; t < kLeaf; ++t) {
+                    int j = j0 + t;
+                    float dx = p.x - q[t].x, dy = p.y - q[t].y, dz = p.z - q[t].z;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float hsum = p.w + q[t].w;
+                    float hs2 = hsum * hsum;
+                    float d = r2 - hs2;
+                    float M = fmaf(c1, hsum, 3.2e-6f * hs2);
+                    bool in = d < -M;
+                    if (fabsf(d) <= M && j < j1 && j != (int)i) {
+                        ++nre;
+                        in = pair_in_fp64(xs[i], ys[i], zs[i], hs[i], xs[j], ys[j], zs[j], hs[j]);
+                    }
+                    if (in && j < j1 && j != (int)i) {
+                        if (cnt < cap) out[cnt] = j;
+                        else over = true;
+                        ++cnt;
+                    }
                 }
             }
         }
-        ncnt[i] = cnt < cap ? cnt : cap;
+        __syncwarp();
+        ncand = 0;
+        if (sp == 0) break;
     }
+    if (valid) ncnt[i] = cnt < cap ? cnt : cap;
     // counters: one atomic per warp
     unsigned long long c = (unsigned long long)(cnt < cap ? cnt : cap);
     for (int o = 16; o > 0; o >>= 1) {
         c += __shfl_xor_sync(0xffffffffu, c, o);
         nre += __shfl_xor_sync(0xffffffffu, nre, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         atomicAdd(&sc->pairs_last, c);
         atomicAdd(&sc->pairs_total, c);
         if (nre) atomicAdd(&sc->rechecks, nre);
@@ -481,6 +583,7 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
                   const TreeLevels &tl, int nleaves, int cap, int fp64_records,
                   cudaStream_t stream, int *nlaunch)
 {
+    const bool multi_star = plan.star_bits > 0;
     const int64_t n = st.n;
     int nl = 0;
     int64_t nb = (n + kBoxThreads - 1) / kBoxThreads;
@@ -492,26 +595,34 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     int gb = (int)((n + tb - 1) / tb);
     k_keys<<<gb, tb, 0, stream>>>(st, s.sc, plan.key_bits_axis, s.keys[0], s.vals[0]);
     ++nl;
+    cudaMemsetAsync(s.radix_tot, 0, sizeof(uint32_t) * 256 * plan.passes, stream);
     for (int p = 0; p < plan.passes; ++p) {
         int src = p & 1, dst = src ^ 1;
         uint32_t *hist = s.hist + (int64_t)p * 256 * plan.nblocks;
+        uint32_t *tot = s.radix_tot + 256 * p;
         k_radix_hist<<<plan.nblocks, kSortThreads, 0, stream>>>(s.keys[src], n, plan.ipt, 8 * p,
-                                                                hist);
-        k_radix_scan<<<1, 1024, 0, stream>>>(hist, plan.nblocks);
+                                                                hist, tot);
+        k_radix_scan<<<256, 256, 0, stream>>>(hist, tot, plan.nblocks);
         k_radix_scatter<<<plan.nblocks, kSortThreads, 0, stream>>>(
             s.keys[src], s.vals[src], s.keys[dst], s.vals[dst], n, plan.ipt, 8 * p, hist);
         nl += 3;
     }
     const uint32_t *order = s.vals[plan.passes & 1];
     k_gather<<<gb, tb, 0, stream>>>(st, order, s.sc, s.perm, s.xs, s.ys, s.zs, s.hs, s.tys, s.rec,
-                                    fp64_records ? s.rec64 : nullptr);
+                                    s.pos4, fp64_records ? s.rec64 : nullptr);
     ++nl;
     k_tree<<<(nleaves + kTreeBlock - 1) / kTreeBlock, kTreeBlock, 0, stream>>>(
         s.xs, s.ys, s.zs, s.hs, s.leaf_start, s.leaf_star, tl, s.nodes, s.sc);
     ++nl;
-    k_neighbors<<<(int)((n + kListThreads - 1) / kListThreads), kListThreads, 0, stream>>>(
-        n, s.rec, s.xs, s.ys, s.zs, s.hs, s.leaf_start, s.leaf_star, s.leaf_of, tl, s.nodes, cap,
-        s.nbr, s.ncnt, s.sc);
+    const int lb = (int)((n + kListThreads - 1) / kListThreads);
+    if (multi_star)
+        k_neighbors<true><<<lb, kListThreads, 0, stream>>>(n, s.pos4, s.xs, s.ys, s.zs, s.hs,
+                                                           s.leaf_start, s.leaf_star, s.leaf_of,
+                                                           tl, s.nodes, cap, s.nbr, s.ncnt, s.sc);
+    else
+        k_neighbors<false><<<lb, kListThreads, 0, stream>>>(n, s.pos4, s.xs, s.ys, s.zs, s.hs,
+                                                            s.leaf_start, s.leaf_star, s.leaf_of,
+                                                            tl, s.nodes, cap, s.nbr, s.ncnt, s.sc);
     ++nl;
     if (nlaunch) *nlaunch += nl;
 }

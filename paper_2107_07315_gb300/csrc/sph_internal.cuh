@@ -29,9 +29,10 @@
 namespace sph {
 
 constexpr int kLeaf = 8;          // particles per tree leaf
-constexpr int kMaxLevels = 32;
-constexpr int kTreeBlock = 256;   // leaves per block in the tree kernel (2^8)
-constexpr int kTreeBlockLevels = 8;
+constexpr int kBranch = 8;        // children per tree node
+constexpr int kMaxLevels = 16;
+constexpr int kTreeBlock = 512;   // leaves per block in the tree kernel (8^3)
+constexpr int kTreeBlockLevels = 3;
 
 // Device error word bits.
 enum : int {
@@ -46,7 +47,10 @@ struct DevScalars {
     unsigned long long bbox_lo[3];   // order-preserving encodings of doubles
     unsigned long long bbox_hi[3];
     double grid;                     // Xhi grid spacing (power of two)
+    double grid_inv;                 // 1/grid (exact)
+    double inv_ext[3];               // 1/(bbox extent) per axis, for Morton keys
     double eps_abs;                  // absolute slack for tree pruning
+    float screen_c1;                 // FP32 screening band coefficient (1.67e-6 max|x|)
     int err;                         // ERR_* bits
     int tree_done;                   // block counter of the tree kernel
     unsigned long long pairs_last;   // ordered pairs of the last RHS
@@ -93,15 +97,39 @@ struct TreeLevels {
     int offset[kMaxLevels];
 };
 
+// Level sizes of the implicit 8-ary tree over nleaves leaves (level 0 =
+// leaves, last level = root).  Returns false if it needs too many levels.
+inline bool make_tree_levels(int nleaves, TreeLevels &tl, int64_t *total_nodes)
+{
+    tl.nlevels = 0;
+    int64_t total = 0;
+    if (nleaves > 0) {
+        int cnt = nleaves;
+        while (true) {
+            if (tl.nlevels >= kMaxLevels) return false;
+            tl.count[tl.nlevels] = cnt;
+            tl.offset[tl.nlevels] = (int)total;
+            total += cnt;
+            tl.nlevels++;
+            if (cnt == 1) break;
+            cnt = (cnt + kBranch - 1) / kBranch;
+        }
+    }
+    if (total_nodes) *total_nodes = total;
+    return true;
+}
+
 // Scratch of one context (device pointers).
 struct Scratch {
     int32_t *perm;
     unsigned long long *keys[2];
     uint32_t *vals[2];
     uint32_t *hist;           // [passes][256][nblocks]
+    uint32_t *radix_tot;      // [8][256] digit totals per pass
     double *xs, *ys, *zs, *hs;
     uint8_t *tys;             // sorted type
     float4 *rec;              // [n][4]
+    float4 *pos4;             // [n] fl32(x, y, z, h) for neighbour screening
     double4_32a *rec64;           // [n][3]
     float4 *sd2;              // [n][2]
     double *sd264;            // [n][8]

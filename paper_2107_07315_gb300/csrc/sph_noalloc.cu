@@ -56,7 +56,9 @@ constexpr size_t kBoxDone = kBoxPart + align256(6 * kBoxBlocksMax * 8);
 constexpr size_t kSc = kBoxDone + 256;
 constexpr size_t kMass = kSc + align256(sizeof(DevScalars));
 constexpr size_t kType = kMass + align256(kMaxN * 8);
-constexpr size_t kBytes = kType + align256(kMaxN);
+constexpr size_t kRadixTot = kType + align256(kMaxN);
+constexpr size_t kPos4 = kRadixTot + align256(8 * 256 * 4);
+constexpr size_t kBytes = kPos4 + align256(kMaxN * 16);
 
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
@@ -135,12 +137,14 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
     s.vals[0] = (uint32_t *)(base + kVals0);
     s.vals[1] = (uint32_t *)(base + kVals1);
     s.hist = (uint32_t *)(base + kHist);
+    s.radix_tot = (uint32_t *)(base + kRadixTot);
     s.xs = (double *)(base + kXs);
     s.ys = (double *)(base + kYs);
     s.zs = (double *)(base + kZs);
     s.hs = (double *)(base + kHs);
     s.tys = base + kTys;
     s.rec = (float4 *)(base + kRec);
+    s.pos4 = (float4 *)(base + kPos4);
     s.nbr = (int32_t *)(base + kNbr);
     s.ncnt = (int32_t *)(base + kNcnt);
     s.nodes = (float4 *)(base + kNodes);
@@ -162,15 +166,7 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
     plan.nblocks = (int)((n + 255) / 256);
     int nleaves = (int)((n + kLeaf - 1) / kLeaf);
     TreeLevels tl{};
-    int cnt = nleaves, total = 0;
-    while (true) {
-        tl.count[tl.nlevels] = cnt;
-        tl.offset[tl.nlevels] = total;
-        total += cnt;
-        tl.nlevels++;
-        if (cnt == 1) break;
-        cnt = (cnt + 1) / 2;
-    }
+    make_tree_levels(nleaves, tl, nullptr);
 
     // Scratch state that must start at zero on every call.
     bool ok = cudaMemsetAsync(s.bbox_done, 0, sizeof(unsigned int), stream) == cudaSuccess &&
