@@ -50,6 +50,20 @@ def dist_env():
     return ws, rank, local
 
 
+def select_stars(st, eos, met, stars):
+    """Particles, EoS and metric tables of the listed stars, renumbered 0..k-1."""
+    stars = list(stars)
+    ids = np.where(np.isin(st["star"], stars))[0]
+    sub = {k: (v[..., ids] if v is not None else None) for k, v in st.items()}
+    remap = {s: i for i, s in enumerate(stars)}
+    sub["star"] = np.array([remap[s] for s in sub["star"]], np.int32)
+    e = {"K": np.asarray(eos["K"])[stars], "Gamma": np.asarray(eos["Gamma"])[stars]}
+    g = dict(met)
+    for k in ("r_max", "alpha", "dalpha", "psi4", "dpsi4", "M", "center"):
+        g[k] = np.asarray(met[k])[stars]
+    return sub, e, g
+
+
 def make_star(seed: int, n: int = N_STAR):
     from paper_2107_07315_gb300 import inputs as I
 
@@ -118,12 +132,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_from_profile(kernel_src: str):
-    """DRAM bytes per force-kernel launch from the committed ncu summary, or
-    None when the kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "force_mixed_star1e5.md")
+PROFILE_FILES = {
+    "force": ("force_mixed_star1e5.md", "sph_pairs.cu"),
+    "density": ("density_mixed_star1e5.md", "sph_pairs.cu"),
+    "lists": ("neighbors_star1e5.md", "sph_build.cu"),
+}
+
+
+def traffic_from_profile(key: str):
+    """DRAM bytes per launch from the committed ncu summary of that kernel,
+    or None when the kernel's source changed since the counters were taken."""
+    name, src = PROFILE_FILES[key]
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
+    kernel_src = os.path.join(ROOT, "paper_2107_07315_gb300", "csrc", src)
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     src_ok, traffic = False, None
     for line in open(path):
@@ -149,7 +172,19 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.device("cuda", torch.cuda.current_device())
-    st, eos, met, dt = make_star(1 + rank, args.n)
+    if args.workload == "ensemble":
+        from paper_2107_07315_gb300 import shard
+
+        # the 64-star ensemble: this rank advances its LPT share of the stars
+        full, eos_all, met_all, params = I.ensemble_state(nstars=args.nstars, seed=2107,
+                                                          scale_n=args.scale, nr=1024)
+        mine = shard.assign_stars(params["N"], ws)[rank]
+        st, eos, met = select_stars(full, eos_all, met_all, mine)
+        dt = 0.5 * I.cfl_dt(st, eos)
+        nst = len(mine)
+    else:
+        st, eos, met, dt = make_star(1 + rank, args.n)
+        nst = 1
     n = len(st["x"])
     prec = sph.SPH_MIXED if args.precision == "mixed" else sph.SPH_FP64
     stream = torch.cuda.Stream()
@@ -234,16 +269,7 @@ def run_ours(args):
         return None
 
     value = pairs / (t_ms * 1e-3)
-    pk, src = peaks()
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    force_ms = tim[0] / max(tim[1], 1)
-    dens_ms = tim[2] / max(tim[3], 1)
-    build_ms = tim[6] / max(tim[7], 1)
-    flops_force = FLOPS_FORCE_PAIR * pairs_step + FLOPS_FORCE_SOLID_EXTRA * solid_pairs
-    achieved = flops_force / (force_ms * 1e-3) / 1e12
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2107_07315_gb300", "csrc",
-                                                "sph_pairs.cu"))
+    rl = rooflines(tim, n, pairs_step, solid_pairs, prec == sph.SPH_MIXED)
     out = {
         "metric": METRIC,
         "value": value,
@@ -258,31 +284,22 @@ def run_ours(args):
         "dtype": "f32" if prec == sph.SPH_MIXED else "f64",
         "data": "synthetic",
         "config": {
-            "workload": "TOV star, %d particles (M=1.4, R=12 km, Gamma=2, 5%% crust), "
-                        "isotropic background, one KDK step per timed step incl. sort and "
-                        "neighbour lists" % n,
+            "workload": ("TOV star, %d particles (M=1.4, R=12 km, Gamma=2, 5%% crust), "
+                         "isotropic background, one KDK step per timed step incl. sort and "
+                         "neighbour lists" % n) if args.workload == "star" else
+                        ("ensemble of %d stars (log-uniform N, Gamma 1.8-2.5, crust 3-10%%), "
+                         "%d particles on this GPU, one launch per kernel for all stars"
+                         % (args.nstars, n)),
             "precision": "mixed: FP32 pair sums (Kahan D, du), FP64 state/integration/totals"
                          if prec == sph.SPH_MIXED else "fp64",
             "n_particles": n,
             "pairs_per_step": pairs_step,
-            "stars_per_gpu": 1,
+            "stars_per_gpu": nst,
             "l2": "flushed between timed steps by a 256 MB write outside the events",
             "parallelism": "independent star per GPU" if ws > 1 else "single GPU",
         },
-        "roofline": {
-            "bound": "alu",
-            "kernel": "force pass (pair sums + finalize)",
-            "achieved": achieved,
-            "peak": peak_tflops,
-            "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops,
-            "traffic": traffic,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, src),
-            "kernel_ms": force_ms,
-            "density_kernel_ms": dens_ms,
-            "neighbour_build_ms": build_ms,
-            "flops_per_launch": flops_force,
-        },
+        "roofline": rl["dominant"],
+        "kernels": rl["all"],
         "gpu_launches": launches,
         "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)},
@@ -294,6 +311,58 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return out
+
+
+def rooflines(tim, n, pairs_step, solid_pairs, mixed):
+    """Roofline entries of the timed kernels; "dominant" is the slowest.
+
+    Algorithmic work per launch:
+      neighbour lists: bytes = 16 n (FP32 positions+h read) + 4 pairs (list
+        entries written) + 4 n (counts written); HBM-bound.
+      density pass: 22 flops per ordered pair; FP32 (FP64) pipe.
+      force pass: 74 flops per ordered pair + 45 for pairs touching a solid
+        particle; FP32 (FP64) pipe.
+    """
+    pk, src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    ms = {
+        "force": tim[0] / max(tim[1], 1),
+        "density": tim[2] / max(tim[3], 1),
+        "lists": tim[8] / max(tim[9], 1),
+    }
+    entries = {}
+    fl = FLOPS_FORCE_PAIR * pairs_step + FLOPS_FORCE_SOLID_EXTRA * solid_pairs
+    a = fl / (ms["force"] * 1e-3) / 1e12 if ms["force"] > 0 else 0.0
+    entries["force"] = {"bound": "alu", "kernel": "k_force_%s (pair sums + finalize)" %
+                        ("mixed" if mixed else "fp64"), "achieved": a, "peak": fp32,
+                        "unit": "TFLOP/s", "frac": a / fp32, "kernel_ms": ms["force"],
+                        "work_per_launch": fl,
+                        "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
+                                       % (sm_mhz, src),
+                        "traffic": traffic_from_profile("force")}
+    fl = FLOPS_DENSITY_PAIR * pairs_step
+    a = fl / (ms["density"] * 1e-3) / 1e12 if ms["density"] > 0 else 0.0
+    entries["density"] = {"bound": "alu", "kernel": "k_density_%s (density sum + EoS)" %
+                          ("mixed" if mixed else "fp64"), "achieved": a, "peak": fp32,
+                          "unit": "TFLOP/s", "frac": a / fp32, "kernel_ms": ms["density"],
+                          "work_per_launch": fl,
+                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s)"
+                                         % (sm_mhz, src),
+                          "traffic": traffic_from_profile("density")}
+    by = 16.0 * n + 4.0 * pairs_step + 4.0 * n
+    a = by / (ms["lists"] * 1e-3) / 1e9 if ms["lists"] > 0 else 0.0
+    entries["lists"] = {"bound": "hbm", "kernel": "k_neighbors (tree walk + exact lists)",
+                        "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                        "kernel_ms": ms["lists"], "work_per_launch": by,
+                        "peak_source": "hbm_gbs (%s)" % src,
+                        "traffic": traffic_from_profile("lists")}
+    dom = max(entries, key=lambda k: entries[k]["kernel_ms"])
+    return {"dominant": entries[dom], "all": {k: {"kernel_ms": v["kernel_ms"],
+                                                  "achieved": v["achieved"], "unit": v["unit"],
+                                                  "frac": v["frac"]} for k, v in entries.items()},
+            "sort_tree_ms": tim[6] / max(tim[7], 1)}
 
 
 def oracle_sample_rhs(st, eos, met, sample: int, seed: int):
@@ -360,7 +429,10 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--n", type=int, default=N_STAR)
-    ap.add_argument("--cpu-sample", type=int, default=400)
+    ap.add_argument("--workload", choices=("star", "ensemble"), default="star")
+    ap.add_argument("--nstars", type=int, default=64)
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--cpu-sample", type=int, default=8000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count-solid", type=int, default=1)
     args = ap.parse_args()

@@ -113,7 +113,9 @@ typedef struct {
  * count is below h_nmin and by 0.9375 above h_nmax [0, 0: off].
  * max_neighbors: per-particle neighbour list capacity [0: 256].
  * lanes_per_particle: 4 or 8 threads share one particle's list in the pair
- * kernels [0: automatic].  use_graph: capture each step in a CUDA graph [1].
+ * kernels [0: 8]; -1 lets sph_init time both on the bound state and keep
+ * the faster (the summation order then depends on that timing).
+ * use_graph: capture each step in a CUDA graph [1].
  * totals_every: compute totals every k steps inside sph_step [0: never]. */
 typedef struct {
     int32_t h_nmin, h_nmax;
@@ -170,14 +172,14 @@ sph_status sph_totals(sph_ctx *ctx, double out[16]);
 sph_status sph_stats(sph_ctx *ctx, int64_t out[16]);
 
 /* Device-time measurement with CUDA events on the context's stream.
- * enable 1 starts recording around the density and force kernels and
- * whole steps; sph_timing_read returns (host out[8]): 0 summed ms of the
- * force kernel, 1 its launches, 2 summed ms of the density kernel, 3 its
- * launches, 4 summed ms of whole steps or right-hand sides, 5 their count,
- * 6 summed ms of neighbour-list construction (sort through list build),
- * 7 its launches.  Reading resets the sums.  Synchronous. */
+ * enable 1 starts recording around the kernels of every step or right-hand
+ * side; sph_timing_read returns (host out[12]) summed milliseconds and
+ * sample counts: 0/1 force kernel, 2/3 density kernel, 4/5 whole steps (or
+ * right-hand sides), 6/7 bounding box through tree (keys, sort, gather,
+ * tree), 8/9 neighbour-list kernel, 10/11 all neighbour search (6 plus 8).
+ * Reading resets the sums.  Synchronous. */
 sph_status sph_timing(sph_ctx *ctx, int32_t enable);
-sph_status sph_timing_read(sph_ctx *ctx, double out[8]);
+sph_status sph_timing_read(sph_ctx *ctx, double out[12]);
 
 /* Checkpoint: the bound particle state plus the rates carried between steps,
  * flags and the step counter, as an opaque host blob.  sph_state_size gives

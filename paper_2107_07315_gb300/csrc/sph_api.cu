@@ -34,8 +34,12 @@ sph_status fail(sph_status st, const char *fmt, ...)
                         "%s: %s", #call, cudaGetErrorString(e_));                        \
     } while (0)
 
+// Timing marks of one step (or one right-hand side): step start, sort+tree
+// start, neighbour-list start, density start, force start, force end, step end.
+enum { EV_STEP, EV_BUILD, EV_LISTS, EV_DENSITY, EV_FORCE, EV_FORCE_END, EV_STEP_END, EV_N };
+
 struct TimingSlot {
-    cudaEvent_t ev[6];  // step start, build start, density start, force start, force end, step end
+    cudaEvent_t ev[EV_N];
 };
 
 }  // namespace
@@ -72,7 +76,7 @@ struct sph_ctx {
     cudaGraphExec_t gexec = nullptr;
     double gdt = 0.0;
     int gtiming = 0;
-    cudaGraphNode_t gev_nodes[6] = {};
+    cudaGraphNode_t gev_nodes[EV_N] = {};
     // timing
     int timing = 0;
     std::vector<TimingSlot> slots;
@@ -181,7 +185,7 @@ sph_status ensure_slot(sph_ctx *c)
     size_t old = c->slots.size();
     c->slots.resize(old + 256);
     for (size_t k = old; k < c->slots.size(); ++k)
-        for (int e = 0; e < 6; ++e) CUDA_TRY(cudaEventCreate(&c->slots[k].ev[e]));
+        for (int e = 0; e < EV_N; ++e) CUDA_TRY(cudaEventCreate(&c->slots[k].ev[e]));
     return SPH_OK;
 }
 
@@ -204,29 +208,74 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
                  int *nlaunch)
 {
     if (c->n == 0) return;
-    rec(c, slot_ev(c, 1), capturing);
+    rec(c, slot_ev(c, EV_BUILD), capturing);
     launch_build(st, c->s, c->plan, c->tl, c->nleaves, c->cap, c->prec == SPH_FP64, c->stream,
-                 nlaunch);
-    rec(c, slot_ev(c, 2), capturing);
+                 nlaunch, slot_ev(c, EV_LISTS), capturing ? 1 : 0);
+    rec(c, slot_ev(c, EV_DENSITY), capturing);
     launch_density(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
                    c->stream);
-    rec(c, slot_ev(c, 3), capturing);
+    rec(c, slot_ev(c, EV_FORCE), capturing);
     launch_force(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
                  c->stream);
-    rec(c, slot_ev(c, 4), capturing);
+    rec(c, slot_ev(c, EV_FORCE_END), capturing);
     if (nlaunch) *nlaunch += 2;
 }
 
 void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch)
 {
     StepState ss = step_state_of(c);
-    rec(c, slot_ev(c, 0), capturing);
+    rec(c, slot_ev(c, EV_STEP), capturing);
     launch_kick_drift(ss, c->r, dt, c->stream);
     DevState st = state_of(c, c->vp, c->vp + c->n, c->vp + 2 * c->n, c->Sp);
     enqueue_rhs(c, st, c->r, capturing, nlaunch);
     launch_kick_return(ss, c->r, eos_of(c), c->mat, dt, c->opt.h_nmin, c->opt.h_nmax, c->stream);
-    rec(c, slot_ev(c, 5), capturing);
+    rec(c, slot_ev(c, EV_STEP_END), capturing);
     if (nlaunch) *nlaunch += 2;
+}
+
+// Autotuner: time the pair kernels with 4 and 8 threads per particle on the
+// bound state (after one neighbour search) and keep the faster.  The choice
+// depends on timing, so two contexts may sum pairs in different orders
+// (results agree to rounding); a fixed lanes_per_particle avoids that.
+sph_status autotune_lanes(sph_ctx *c)
+{
+    DevState st = state_of(c, c->P.vx, c->P.vy, c->P.vz, c->P.S);
+    int timing = c->timing;
+    c->timing = 0;
+    enqueue_rhs(c, st, c->r, false, nullptr);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best = 3e38f;
+    int best_lanes = 8;
+    for (int lanes : {4, 8}) {
+        c->lanes = lanes;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, c->stream);
+            launch_density(st, c->s, eos_of(c), c->met, c->r, c->cap, lanes, c->prec == SPH_FP64,
+                           c->stream);
+            launch_force(st, c->s, eos_of(c), c->mat, c->met, c->r, c->cap, lanes,
+                         c->prec == SPH_FP64, c->stream);
+        }
+        cudaEventRecord(e1, c->stream);
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(SPH_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+        }
+        if (ms < best) {
+            best = ms;
+            best_lanes = lanes;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->lanes = best_lanes;
+    c->timing = timing;
+    return SPH_OK;
 }
 
 void drop_graph(sph_ctx *c)
@@ -257,7 +306,7 @@ sph_status capture_step(sph_ctx *c, double dt)
         c->gexec = nullptr;
         return fail(SPH_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     }
-    for (int k = 0; k < 6; ++k) c->gev_nodes[k] = nullptr;
+    for (int k = 0; k < EV_N; ++k) c->gev_nodes[k] = nullptr;
     if (c->timing) {
         size_t nn = 0;
         cudaGraphGetNodes(graph, nullptr, &nn);
@@ -269,7 +318,7 @@ sph_status capture_step(sph_ctx *c, double dt)
             if (ty != cudaGraphNodeTypeEventRecord) continue;
             cudaEvent_t ev;
             cudaGraphEventRecordNodeGetEvent(nd, &ev);
-            for (int k = 0; k < 6; ++k)
+            for (int k = 0; k < EV_N; ++k)
                 if (ev == c->slots[saved_used].ev[k]) c->gev_nodes[k] = nd;
         }
     }
@@ -325,8 +374,8 @@ sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_materi
         if (opt->max_neighbors < 0 || opt->max_neighbors > 4096)
             return fail(SPH_ERR_ARG, "max_neighbors out of range");
         if (opt->lanes_per_particle != 0 && opt->lanes_per_particle != 4 &&
-            opt->lanes_per_particle != 8)
-            return fail(SPH_ERR_ARG, "lanes_per_particle must be 0, 4 or 8");
+            opt->lanes_per_particle != 8 && opt->lanes_per_particle != -1)
+            return fail(SPH_ERR_ARG, "lanes_per_particle must be -1, 0, 4 or 8");
         if (opt->h_nmax < 0 || opt->h_nmin < 0 || (opt->h_nmax > 0 && opt->h_nmin > opt->h_nmax))
             return fail(SPH_ERR_ARG, "h_nmin/h_nmax band invalid");
     }
@@ -502,6 +551,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
         c->met.center = d_center;
     }
     CUDA_TRY(cudaDeviceSynchronize());
+    if (c->opt.lanes_per_particle == -1 && n > 0) STATUS_TRY(autotune_lanes(c));
     return SPH_OK;
 }
 
@@ -590,7 +640,7 @@ sph_status sph_step(sph_ctx *c, double dt, int32_t nsteps)
         if (graph) {
             if (!c->gexec || c->gdt != dt || c->gtiming != c->timing) STATUS_TRY(capture_step(c, dt));
             if (c->timing) {
-                for (int e = 0; e < 6; ++e)
+                for (int e = 0; e < EV_N; ++e)
                     if (c->gev_nodes[e])
                         CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->gev_nodes[e],
                                                                       c->slots[c->slot_used].ev[e]));
@@ -690,33 +740,26 @@ sph_status sph_timing(sph_ctx *c, int32_t enable)
     return SPH_OK;
 }
 
-sph_status sph_timing_read(sph_ctx *c, double out[8])
+sph_status sph_timing_read(sph_ctx *c, double out[12])
 {
     if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    for (int k = 0; k < 8; ++k) out[k] = 0.0;
-    for (int k = 0; k < c->slot_used; ++k) {
+    for (int k = 0; k < 12; ++k) out[k] = 0.0;
+    auto add = [&](const TimingSlot &s, int a, int b, int k) -> bool {
         float ms = 0.f;
-        TimingSlot &s = c->slots[k];
-        if (cudaEventElapsedTime(&ms, s.ev[3], s.ev[4]) == cudaSuccess) {
-            out[0] += ms;
-            out[1] += 1;
-        }
-        if (cudaEventElapsedTime(&ms, s.ev[2], s.ev[3]) == cudaSuccess) {
-            out[2] += ms;
-            out[3] += 1;
-        }
-        if (cudaEventElapsedTime(&ms, s.ev[0], s.ev[5]) == cudaSuccess) {
-            out[4] += ms;
-            out[5] += 1;
-        } else if (cudaEventElapsedTime(&ms, s.ev[1], s.ev[4]) == cudaSuccess) {
-            out[4] += ms;
-            out[5] += 1;
-        }
-        if (cudaEventElapsedTime(&ms, s.ev[1], s.ev[2]) == cudaSuccess) {
-            out[6] += ms;
-            out[7] += 1;
-        }
+        if (cudaEventElapsedTime(&ms, s.ev[a], s.ev[b]) != cudaSuccess) return false;
+        out[k] += ms;
+        out[k + 1] += 1;
+        return true;
+    };
+    for (int k = 0; k < c->slot_used; ++k) {
+        const TimingSlot &s = c->slots[k];
+        add(s, EV_FORCE, EV_FORCE_END, 0);
+        add(s, EV_DENSITY, EV_FORCE, 2);
+        if (!add(s, EV_STEP, EV_STEP_END, 4)) add(s, EV_BUILD, EV_FORCE_END, 4);
+        add(s, EV_BUILD, EV_LISTS, 6);
+        add(s, EV_LISTS, EV_DENSITY, 8);
+        add(s, EV_BUILD, EV_DENSITY, 10);
     }
     cudaGetLastError();
     c->slot_used = 0;
@@ -798,7 +841,7 @@ void sph_free(sph_ctx *c)
     else cudaDeviceSynchronize();
     drop_graph(c);
     for (auto &s : c->slots)
-        for (int e = 0; e < 6; ++e) cudaEventDestroy(s.ev[e]);
+        for (int e = 0; e < EV_N; ++e) cudaEventDestroy(s.ev[e]);
     for (void *p : c->allocs) cudaFree(p);
     cudaGetLastError();
     delete c;

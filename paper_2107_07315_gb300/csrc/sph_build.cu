@@ -127,6 +127,7 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
         sc->screen_c1 = (float)(1.67e-6 * m);
         sc->pairs_last = 0ull;
         sc->tree_done = 0;
+        sc->list_next = 0u;
         sc->rhs_count += 1ull;
         *done = 0u;
     }
@@ -445,11 +446,22 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
     __shared__ int s_leaf[kListWarps][kCandCap];
     __shared__ unsigned s_mask[kListWarps][kCandCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const float c1 = sc->screen_c1;
+    const float eps = (float)sc->eps_abs;
+    const int64_t ngroups = (n + 31) / 32;
+    unsigned long long nre = 0, pairs = 0;
+    bool over = false;
+    // Persistent warps: each claims the next group of 32 sorted particles
+    // from a counter (reset at the start of every right-hand side), which
+    // evens out the uneven cost of groups across the SMs.
+    while (true) {
+    int64_t grp = 0;
+    if (lane == 0) grp = (int64_t)atomicAdd(&sc->list_next, 1u);
+    grp = __shfl_sync(0xffffffffu, grp, 0);
+    if (grp >= ngroups) break;
+    const int64_t i = grp * 32 + lane;
     const bool valid = i < n;
     int cnt = 0;
-    unsigned long long nre = 0;
-    bool over = false;
     // invalid lanes sit far away: every box and pair test fails for them
     float4 p = make_float4(3e38f, 3e38f, 3e38f, 0.f);
     int star = 0;
@@ -457,8 +469,6 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
         p = pos4[i];
         if (MULTI_STAR) star = leaf_star[leaf_of[i]];
     }
-    const float c1 = sc->screen_c1;
-    const float eps = (float)sc->eps_abs;
     int32_t *out = nbr + i * (int64_t)cap;
 
     auto box_hit = [&](const float4 &a, const float4 &b) -> bool {
@@ -562,8 +572,10 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
         if (sp == 0) break;
     }
     if (valid) ncnt[i] = cnt < cap ? cnt : cap;
+    pairs += (unsigned long long)(cnt < cap ? cnt : cap);
+    }  // group loop
     // counters: one atomic per warp
-    unsigned long long c = (unsigned long long)(cnt < cap ? cnt : cap);
+    unsigned long long c = pairs;
     for (int o = 16; o > 0; o >>= 1) {
         c += __shfl_xor_sync(0xffffffffu, c, o);
         nre += __shfl_xor_sync(0xffffffffu, nre, o);
@@ -581,7 +593,7 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
 // Host-side launch sequence of the neighbour search.
 void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
                   const TreeLevels &tl, int nleaves, int cap, int fp64_records,
-                  cudaStream_t stream, int *nlaunch)
+                  cudaStream_t stream, int *nlaunch, cudaEvent_t ev_lists, int ev_external)
 {
     const bool multi_star = plan.star_bits > 0;
     const int64_t n = st.n;
@@ -614,7 +626,23 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     k_tree<<<(nleaves + kTreeBlock - 1) / kTreeBlock, kTreeBlock, 0, stream>>>(
         s.xs, s.ys, s.zs, s.hs, s.leaf_start, s.leaf_star, tl, s.nodes, s.sc);
     ++nl;
-    const int lb = (int)((n + kListThreads - 1) / kListThreads);
+    if (ev_lists) {
+        if (ev_external) cudaEventRecordWithFlags(ev_lists, stream, cudaEventRecordExternal);
+        else cudaEventRecord(ev_lists, stream);
+    }
+    // persistent grid: enough warps to fill every SM, never more than groups
+    static int sms = 0, per_sm_t = 0, per_sm_f = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_neighbors<true>, kListThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_neighbors<false>, kListThreads, 0);
+        if (sms < 1) sms = 1;
+    }
+    const int64_t need = (n + kListThreads - 1) / kListThreads;
+    int64_t cap_blocks = (int64_t)sms * ((multi_star ? per_sm_t : per_sm_f) > 0 ? (multi_star ? per_sm_t : per_sm_f) : 1);
+    const int lb = (int)(need < cap_blocks ? need : cap_blocks);
     if (multi_star)
         k_neighbors<true><<<lb, kListThreads, 0, stream>>>(n, s.pos4, s.xs, s.ys, s.zs, s.hs,
                                                            s.leaf_start, s.leaf_star, s.leaf_of,

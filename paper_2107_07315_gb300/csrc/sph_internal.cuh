@@ -53,6 +53,7 @@ struct DevScalars {
     float screen_c1;                 // FP32 screening band coefficient (1.67e-6 max|x|)
     int err;                         // ERR_* bits
     int tree_done;                   // block counter of the tree kernel
+    unsigned int list_next;          // next particle group of the neighbour kernel
     unsigned long long pairs_last;   // ordered pairs of the last RHS
     unsigned long long pairs_total;
     unsigned long long rechecks;     // marginal FP64 predicate evaluations
@@ -157,9 +158,12 @@ struct SortPlan {
 
 constexpr int kBoxBlocksMax = 304;
 
+// ev_lists (optional) is recorded between the tree and the neighbour-list
+// kernels; ev_external marks a record inside a stream capture.
 void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
                   const TreeLevels &tl, int nleaves, int cap, int fp64_records,
-                  cudaStream_t stream, int *nlaunch);
+                  cudaStream_t stream, int *nlaunch, cudaEvent_t ev_lists = nullptr,
+                  int ev_external = 0);
 
 void launch_density(const DevState &st, const Scratch &s, const DevEos &eos,
                     const DevMetric &g, const DevRates &out, int cap, int lanes, int fp64,

@@ -122,61 +122,79 @@ __device__ __forceinline__ Prep<T> eos_prep(const DevEos &eos, const DevMetric &
     return p;
 }
 
+// Block layout shared by the pair kernels: a block owns kPB consecutive
+// sorted particles.  Phase 1 runs the pair sums: LPI threads share one
+// particle's list, kPB/LPI particles per round, LPI rounds; the group's sums
+// are combined with xor shuffles (fixed order) and parked in shared memory.
+// Phase 2 gives every thread one particle for the per-particle work (EoS,
+// finalize) at full SIMD width.
+constexpr int kPB = 128;    // particles (and threads) per block, mixed precision
+constexpr int kPB64 = 64;   // particles (and threads) per block, FP64
+
 // ------------------------------------------------------------------ density
 template <int LPI>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kPB)
 k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRates out, int cap)
 {
+    __shared__ float s_D[kPB];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
-    const bool valid = i < n;
-    const int cnt = valid ? s.ncnt[i] : 0;
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) {
-        a0 = s.rec[i * 4 + 0];
-        a1 = s.rec[i * 4 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kPB;
+#pragma unroll 1
+    for (int r = 0; r < LPI; ++r) {
+        const int slot = r * (kPB / LPI) + grp;
+        const int64_t i = base + slot;
+        const bool valid = i < n;
+        const int cnt = valid ? s.ncnt[i] : 0;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            a0 = s.rec[i * 4 + 0];
+            a1 = s.rec[i * 4 + 1];
+        }
+        float sum = 0.f, comp = 0.f;
+        const int32_t *list = s.nbr + i * (int64_t)cap;
+        for (int k = sub; k < cnt; k += LPI) {
+            int j = list[k];
+            float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
+            float dx = (a0.x - q0.x) + (a1.x - q1.x);
+            float dy = (a0.y - q0.y) + (a1.y - q1.y);
+            float dz = (a0.z - q0.z) + (a1.z - q1.z);
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float hab = 0.5f * (a0.w + q0.w);
+            float hinv = __frcp_rn(hab);
+            float q = sqrtf(r2) * hinv;
+            float sig = hinv * hinv * hinv * kInvPiF;
+            float t = 2.f - q;
+            float W = q < 1.f ? sig * fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.f) : sig * 0.25f * t * t * t;
+            float term = q1.w * W;
+            float y = term - comp;
+            float tt = sum + y;
+            comp = (tt - sum) - y;
+            sum = tt;
+        }
+        for (int o = LPI / 2; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            comp += __shfl_xor_sync(0xffffffffu, comp, o);
+        }
+        if (sub == 0) {
+            float hi = a0.w;
+            s_D[slot] = valid ? a1.w * kInvPiF / (hi * hi * hi) + (sum - comp) : 1.f;
+        }
     }
-    float sum = 0.f, comp = 0.f;
-    const int32_t *list = s.nbr + i * (int64_t)cap;
-    for (int k = sub; k < cnt; k += LPI) {
-        int j = list[k];
-        float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
-        float dx = (a0.x - q0.x) + (a1.x - q1.x);
-        float dy = (a0.y - q0.y) + (a1.y - q1.y);
-        float dz = (a0.z - q0.z) + (a1.z - q1.z);
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float hab = 0.5f * (a0.w + q0.w);
-        float hinv = __frcp_rn(hab);
-        float q = sqrtf(r2) * hinv;
-        float sig = hinv * hinv * hinv * kInvPiF;
-        float t = 2.f - q;
-        float W = q < 1.f ? sig * fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.f) : sig * 0.25f * t * t * t;
-        float term = q1.w * W;
-        float y = term - comp;
-        float tt = sum + y;
-        comp = (tt - sum) - y;
-        sum = tt;
-    }
-    for (int o = LPI / 2; o > 0; o >>= 1) {
-        sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        comp += __shfl_xor_sync(0xffffffffu, comp, o);
-    }
-    if (!valid) return;
-    float hi = a0.w;
-    float self = a1.w * kInvPiF / (hi * hi * hi);
-    float D = self + (sum - comp);
-    int c = s.perm[i];
-    int star = st.star ? st.star[c] : 0;
-    float vx = (float)st.vx[c], vy = (float)st.vy[c], vz = (float)st.vz[c];
+    __syncthreads();
+    const int64_t i = base + threadIdx.x;
+    if (i >= n) return;
+    const float D = s_D[threadIdx.x];
+    const int c = s.perm[i];
+    const int star = st.star ? st.star[c] : 0;
+    const float vx = (float)st.vx[c], vy = (float)st.vy[c], vz = (float)st.vz[c];
     Prep<float> p = eos_prep<float>(eos, g, star, D, vx, vy, vz, s.xs[i], s.ys[i], s.zs[i]);
-    if (sub != 0) return;
-    float invD = 1.f / D;
-    float PD2 = p.P * invD * invD;
+    const float invD = 1.f / D;
+    const float PD2 = p.P * invD * invD;
     s.rec[i * 4 + 2] = make_float4(vx, vy, vz, D);
     s.rec[i * 4 + 3] = make_float4(PD2, p.cs, invD, 0.f);
     if (s.tys[i] == 1) {
         const int64_t N = st.n;
-        float f = invD * invD;
+        const float f = invD * invD;
         s.sd2[i * 2 + 0] = make_float4((float)st.S[c] * f, (float)st.S[N + c] * f,
                                        (float)st.S[2 * N + c] * f, (float)st.S[3 * N + c] * f);
         s.sd2[i * 2 + 1] = make_float4((float)st.S[4 * N + c] * f, (float)st.S[5 * N + c] * f,
@@ -191,58 +209,70 @@ k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevR
     out.rho[c] = p.rho;
     out.P[c] = p.P;
     out.cs[c] = p.cs;
-    out.ncount[c] = cnt;
+    out.ncount[c] = s.ncnt[i];
 }
 
 template <int LPI>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kPB64)
 k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRates out, int cap)
 {
+    __shared__ double s_D[kPB64];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
-    const bool valid = i < n;
-    const int cnt = valid ? s.ncnt[i] : 0;
-    double4_32a a0 = make_double4_32a(0, 0, 0, 1);
-    double mi = 0.0;
-    if (valid) {
-        a0 = s.rec64[i * 3 + 0];
-        mi = s.rec64[i * 3 + 1].x;
-    }
-    double sum = 0.0;
-    const int32_t *list = s.nbr + i * (int64_t)cap;
-    for (int k = sub; k < cnt; k += LPI) {
-        int j = list[k];
-        double4_32a q0 = s.rec64[(int64_t)j * 3 + 0];
-        double mj = s.rec64[(int64_t)j * 3 + 1].x;
-        double dx = a0.x - q0.x, dy = a0.y - q0.y, dz = a0.z - q0.z;
-        double r = sqrt(dx * dx + dy * dy + dz * dz);
-        double hab = 0.5 * (a0.w + q0.w);
-        double q = r / hab;
-        double sig = 1.0 / (kPi * hab * hab * hab);
-        double W;
-        if (q < 1.0) W = sig * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
-        else {
-            double t = 2.0 - q;
-            W = sig * 0.25 * t * t * t;
+    const int64_t base = (int64_t)blockIdx.x * kPB64;
+#pragma unroll 1
+    for (int r = 0; r < LPI; ++r) {
+        const int slot = r * (kPB64 / LPI) + grp;
+        const int64_t i = base + slot;
+        const bool valid = i < n;
+        const int cnt = valid ? s.ncnt[i] : 0;
+        double4_32a a0 = make_double4_32a(0, 0, 0, 1);
+        double mi = 0.0;
+        if (valid) {
+            a0 = s.rec64[i * 3 + 0];
+            mi = s.rec64[i * 3 + 1].x;
         }
-        sum += mj * W;
+        double sum = 0.0;
+        const int32_t *list = s.nbr + i * (int64_t)cap;
+        for (int k = sub; k < cnt; k += LPI) {
+            int j = list[k];
+            double4_32a q0 = s.rec64[(int64_t)j * 3 + 0];
+            double mj = s.rec64[(int64_t)j * 3 + 1].x;
+            double dx = a0.x - q0.x, dy = a0.y - q0.y, dz = a0.z - q0.z;
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double hab = 0.5 * (a0.w + q0.w);
+            double q = r / hab;
+            double sig = 1.0 / (kPi * hab * hab * hab);
+            double W;
+            if (q < 1.0) W = sig * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+            else {
+                double t = 2.0 - q;
+                W = sig * 0.25 * t * t * t;
+            }
+            sum += mj * W;
+        }
+        for (int o = LPI / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (sub == 0) {
+            double hi = a0.w;
+            s_D[slot] = valid ? mi / (kPi * hi * hi * hi) + sum : 1.0;
+        }
     }
-    for (int o = LPI / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (!valid) return;
-    double hi = a0.w;
-    double D = mi / (kPi * hi * hi * hi) + sum;
-    int c = s.perm[i];
-    int star = st.star ? st.star[c] : 0;
-    double vx = st.vx[c], vy = st.vy[c], vz = st.vz[c];
+    __syncthreads();
+    const int64_t i = base + threadIdx.x;
+    if (i >= n) return;
+    const double D = s_D[threadIdx.x];
+    const double4_32a a0 = s.rec64[i * 3 + 0];
+    const double mi = s.rec64[i * 3 + 1].x;
+    const int c = s.perm[i];
+    const int star = st.star ? st.star[c] : 0;
+    const double vx = st.vx[c], vy = st.vy[c], vz = st.vz[c];
     Prep<double> p = eos_prep<double>(eos, g, star, D, vx, vy, vz, a0.x, a0.y, a0.z);
-    if (sub != 0) return;
-    double invD = 1.0 / D;
-    double PD2 = p.P / (D * D);
+    const double invD = 1.0 / D;
+    const double PD2 = p.P / (D * D);
     s.rec64[i * 3 + 1] = make_double4_32a(mi, vx, vy, vz);
     s.rec64[i * 3 + 2] = make_double4_32a(D, invD, PD2, p.cs);
     double *sd = s.sd264 + i * 8;
     const int64_t N = st.n;
-    bool solid = s.tys[i] == 1;
+    const bool solid = s.tys[i] == 1;
     for (int k = 0; k < 6; ++k) sd[k] = solid ? st.S[k * N + c] / (D * D) : 0.0;
     double *q = s.pp64 + i * 8;
     q[0] = p.rho; q[1] = p.P; q[2] = p.cP; q[3] = p.henth; q[4] = p.Wt; q[5] = p.cs; q[6] = D;
@@ -250,7 +280,7 @@ k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRa
     out.rho[c] = p.rho;
     out.P[c] = p.P;
     out.cs[c] = p.cs;
-    out.ncount[c] = cnt;
+    out.ncount[c] = s.ncnt[i];
 }
 
 // -------------------------------------------------------------- finalize
@@ -331,211 +361,248 @@ __device__ __forceinline__ void finalize(int64_t i, int c, int64_t N, const DevS
 }
 
 // ------------------------------------------------------------------- force
+// Reduced pair sums per particle, in the order stored in shared memory.
+enum { A_P0, A_P1, A_P2, A_X0, A_X1, A_X2, A_DU, A_DUC, A_DD, A_G00, A_G01, A_G02, A_G10, A_G11,
+       A_G12, A_G20, A_G21, A_G22, A_N };
+
 template <int LPI>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kPB)
 k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
               DevRates out, int cap)
 {
     (void)eos;
+    __shared__ float s_acc[A_N][kPB];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
-    const bool valid = i < n;
-    const int cnt = valid ? s.ncnt[i] : 0;
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = a0, a2 = make_float4(0.f, 0.f, 0.f, 1.f),
-           a3 = make_float4(0.f, 0.f, 1.f, 0.f), as0 = make_float4(0.f, 0.f, 0.f, 0.f), as1 = as0;
-    bool solid_i = false;
-    if (valid) {
-        a0 = s.rec[i * 4 + 0];
-        a1 = s.rec[i * 4 + 1];
-        a2 = s.rec[i * 4 + 2];
-        a3 = s.rec[i * 4 + 3];
-        solid_i = s.tys[i] == 1;
-        if (solid_i) {
-            as0 = s.sd2[i * 2 + 0];
-            as1 = s.sd2[i * 2 + 1];
-        }
-    }
+    const int64_t base = (int64_t)blockIdx.x * kPB;
     const float alpha_av = (float)mat.alpha_av, beta_av = (float)mat.beta_av;
     const float eta2 = (float)mat.eta2;
-    float aP0 = 0.f, aP1 = 0.f, aP2 = 0.f, aX0 = 0.f, aX1 = 0.f, aX2 = 0.f;
-    float du = 0.f, duc = 0.f, dD = 0.f;
-    float G00 = 0.f, G01 = 0.f, G02 = 0.f, G10 = 0.f, G11 = 0.f, G12 = 0.f, G20 = 0.f, G21 = 0.f,
-          G22 = 0.f;
-    const int32_t *list = s.nbr + i * (int64_t)cap;
-    for (int k = sub; k < cnt; k += LPI) {
-        const int j = list[k];
-        const float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
-        const float4 q2 = s.rec[(int64_t)j * 4 + 2], q3 = s.rec[(int64_t)j * 4 + 3];
-        const bool solid_j = s.tys[j] == 1;
-        float dx = (a0.x - q0.x) + (a1.x - q1.x);
-        float dy = (a0.y - q0.y) + (a1.y - q1.y);
-        float dz = (a0.z - q0.z) + (a1.z - q1.z);
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float r2c = fmaxf(r2, 1.17549435e-38f);
-        float rinv = rsqrtf(r2c);
-        float r = r2c * rinv;
-        float hab = 0.5f * (a0.w + q0.w);
-        float hinv = __frcp_rn(hab);
-        float q = r * hinv;
-        float hinv2 = hinv * hinv;
-        float s5 = hinv2 * hinv2 * hinv * kInvPiF;
-        float t = 2.f - q;
-        float gW = q < 1.f ? s5 * fmaf(2.25f, q, -3.f) : -0.75f * s5 * t * t * hab * rinv;
-        float w = q1.w * gW;
-        float dvx = a2.x - q2.x, dvy = a2.y - q2.y, dvz = a2.z - q2.z;
-        float vdx = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
-        float Pi = 0.f;
-        if (vdx < 0.f) {
-            float mu = hab * vdx / fmaf(eta2 * hab, hab, r2);
-            float cbar = 0.5f * (a3.y + q3.y);
-            Pi = fmaf(-alpha_av * cbar, mu, beta_av * mu * mu) * (2.f / (a2.w + q2.w));
-        }
-        float fp = (a3.x + q3.x) * w;
-        float fv = Pi * w;
-        aP0 = fmaf(-fp, dx, aP0);
-        aP1 = fmaf(-fp, dy, aP1);
-        aP2 = fmaf(-fp, dz, aP2);
-        aX0 = fmaf(-fv, dx, aX0);
-        aX1 = fmaf(-fv, dy, aX1);
-        aX2 = fmaf(-fv, dz, aX2);
-        float vw = vdx * w;
-        float term = fmaf(0.5f, Pi, a3.x) * vw;
-        float yk = term - duc;
-        float tk = du + yk;
-        duc = (tk - du) - yk;
-        du = tk;
-        dD = fmaf(vw, q3.z, dD);
-        if (solid_i || solid_j) {
-            float wx = w * dx, wy = w * dy, wz = w * dz;
-            float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
-            if (solid_j) {
-                b0 = s.sd2[(int64_t)j * 2 + 0];
-                b1 = s.sd2[(int64_t)j * 2 + 1];
-            }
-            float Txx = as0.x + b0.x, Tyy = as0.y + b0.y, Tzz = as0.z + b0.z;
-            float Txy = as0.w + b0.w, Txz = as1.x + b1.x, Tyz = as1.y + b1.y;
-            aX0 = fmaf(Txx, wx, fmaf(Txy, wy, fmaf(Txz, wz, aX0)));
-            aX1 = fmaf(Txy, wx, fmaf(Tyy, wy, fmaf(Tyz, wz, aX1)));
-            aX2 = fmaf(Txz, wx, fmaf(Tyz, wy, fmaf(Tzz, wz, aX2)));
+#pragma unroll 1
+    for (int r = 0; r < LPI; ++r) {
+        const int slot = r * (kPB / LPI) + grp;
+        const int64_t i = base + slot;
+        const bool valid = i < n;
+        const int cnt = valid ? s.ncnt[i] : 0;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = a0, a2 = make_float4(0.f, 0.f, 0.f, 1.f),
+               a3 = make_float4(0.f, 0.f, 1.f, 0.f), as0 = make_float4(0.f, 0.f, 0.f, 0.f),
+               as1 = as0;
+        bool solid_i = false;
+        if (valid) {
+            a0 = s.rec[i * 4 + 0];
+            a1 = s.rec[i * 4 + 1];
+            a2 = s.rec[i * 4 + 2];
+            a3 = s.rec[i * 4 + 3];
+            solid_i = s.tys[i] == 1;
             if (solid_i) {
-                G00 = fmaf(-dvx, wx, G00); G01 = fmaf(-dvx, wy, G01); G02 = fmaf(-dvx, wz, G02);
-                G10 = fmaf(-dvy, wx, G10); G11 = fmaf(-dvy, wy, G11); G12 = fmaf(-dvy, wz, G12);
-                G20 = fmaf(-dvz, wx, G20); G21 = fmaf(-dvz, wy, G21); G22 = fmaf(-dvz, wz, G22);
+                as0 = s.sd2[i * 2 + 0];
+                as1 = s.sd2[i * 2 + 1];
             }
         }
+        float aP0 = 0.f, aP1 = 0.f, aP2 = 0.f, aX0 = 0.f, aX1 = 0.f, aX2 = 0.f;
+        float du = 0.f, duc = 0.f, dD = 0.f;
+        float G00 = 0.f, G01 = 0.f, G02 = 0.f, G10 = 0.f, G11 = 0.f, G12 = 0.f, G20 = 0.f,
+              G21 = 0.f, G22 = 0.f;
+        const int32_t *list = s.nbr + i * (int64_t)cap;
+        for (int k = sub; k < cnt; k += LPI) {
+            const int j = list[k];
+            const float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
+            const float4 q2 = s.rec[(int64_t)j * 4 + 2], q3 = s.rec[(int64_t)j * 4 + 3];
+            const bool solid_j = s.tys[j] == 1;
+            float dx = (a0.x - q0.x) + (a1.x - q1.x);
+            float dy = (a0.y - q0.y) + (a1.y - q1.y);
+            float dz = (a0.z - q0.z) + (a1.z - q1.z);
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float r2c = fmaxf(r2, 1.17549435e-38f);
+            float rinv = rsqrtf(r2c);
+            float r = r2c * rinv;
+            float hab = 0.5f * (a0.w + q0.w);
+            float hinv = __frcp_rn(hab);
+            float q = r * hinv;
+            float hinv2 = hinv * hinv;
+            float s5 = hinv2 * hinv2 * hinv * kInvPiF;
+            float t = 2.f - q;
+            float gW = q < 1.f ? s5 * fmaf(2.25f, q, -3.f) : -0.75f * s5 * t * t * hab * rinv;
+            float w = q1.w * gW;
+            float dvx = a2.x - q2.x, dvy = a2.y - q2.y, dvz = a2.z - q2.z;
+            float vdx = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
+            // Monaghan viscosity, zero for receding pairs (select, no branch)
+            float muv = __fdividef(hab * vdx, fmaf(eta2 * hab, hab, r2));
+            muv = vdx < 0.f ? muv : 0.f;
+            float cbar = 0.5f * (a3.y + q3.y);
+            float Pi = fmaf(-alpha_av * cbar, muv, beta_av * muv * muv) *
+                       __fdividef(2.f, a2.w + q2.w);
+            float fp = (a3.x + q3.x) * w;
+            float fv = Pi * w;
+            aP0 = fmaf(-fp, dx, aP0);
+            aP1 = fmaf(-fp, dy, aP1);
+            aP2 = fmaf(-fp, dz, aP2);
+            aX0 = fmaf(-fv, dx, aX0);
+            aX1 = fmaf(-fv, dy, aX1);
+            aX2 = fmaf(-fv, dz, aX2);
+            float vw = vdx * w;
+            float term = fmaf(0.5f, Pi, a3.x) * vw;
+            float yk = term - duc;
+            float tk = du + yk;
+            duc = (tk - du) - yk;
+            du = tk;
+            dD = fmaf(vw, q3.z, dD);
+            if (solid_i || solid_j) {
+                float wx = w * dx, wy = w * dy, wz = w * dz;
+                float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+                if (solid_j) {
+                    b0 = s.sd2[(int64_t)j * 2 + 0];
+                    b1 = s.sd2[(int64_t)j * 2 + 1];
+                }
+                float Txx = as0.x + b0.x, Tyy = as0.y + b0.y, Tzz = as0.z + b0.z;
+                float Txy = as0.w + b0.w, Txz = as1.x + b1.x, Tyz = as1.y + b1.y;
+                aX0 = fmaf(Txx, wx, fmaf(Txy, wy, fmaf(Txz, wz, aX0)));
+                aX1 = fmaf(Txy, wx, fmaf(Tyy, wy, fmaf(Tyz, wz, aX1)));
+                aX2 = fmaf(Txz, wx, fmaf(Tyz, wy, fmaf(Tzz, wz, aX2)));
+                if (solid_i) {
+                    G00 = fmaf(-dvx, wx, G00); G01 = fmaf(-dvx, wy, G01); G02 = fmaf(-dvx, wz, G02);
+                    G10 = fmaf(-dvy, wx, G10); G11 = fmaf(-dvy, wy, G11); G12 = fmaf(-dvy, wz, G12);
+                    G20 = fmaf(-dvz, wx, G20); G21 = fmaf(-dvz, wy, G21); G22 = fmaf(-dvz, wz, G22);
+                }
+            }
+        }
+        float acc[A_N] = {aP0, aP1, aP2, aX0, aX1, aX2, du, duc, dD,
+                          G00, G01, G02, G10, G11, G12, G20, G21, G22};
+#pragma unroll
+        for (int a = 0; a < A_N; ++a) {
+            float v = acc[a];
+            for (int o = LPI / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (sub == 0) s_acc[a][slot] = v;
+        }
     }
-#define SPH_RED(v) v += __shfl_xor_sync(0xffffffffu, v, o)
-    for (int o = LPI / 2; o > 0; o >>= 1) {
-        SPH_RED(aP0); SPH_RED(aP1); SPH_RED(aP2); SPH_RED(aX0); SPH_RED(aX1); SPH_RED(aX2);
-        SPH_RED(du); SPH_RED(duc); SPH_RED(dD);
-        SPH_RED(G00); SPH_RED(G01); SPH_RED(G02); SPH_RED(G10); SPH_RED(G11); SPH_RED(G12);
-        SPH_RED(G20); SPH_RED(G21); SPH_RED(G22);
-    }
-#undef SPH_RED
-    if (!valid || sub != 0) return;
+    __syncthreads();
+    const int64_t i = base + threadIdx.x;
+    if (i >= n) return;
+    const int t = threadIdx.x;
     const int c = s.perm[i];
     const int star = st.star ? st.star[c] : 0;
+    const float4 a2 = s.rec[i * 4 + 2];
     const float4 p0 = s.pp[i * 2 + 0], p1 = s.pp[i * 2 + 1];
-    float aP[3] = {aP0, aP1, aP2}, aX[3] = {aX0, aX1, aX2};
-    float G[3][3] = {{G00, G01, G02}, {G10, G11, G12}, {G20, G21, G22}};
-    finalize<float>(i, c, st.n, st, mat, g, star, solid_i, a2.w, aP, aX, du - duc, dD, G, p0.x,
-                    p0.z, p0.w, p1.x, a2.x, a2.y, a2.z, s.xs[i], s.ys[i], s.zs[i], out);
+    const bool solid_i = s.tys[i] == 1;
+    float aP[3] = {s_acc[A_P0][t], s_acc[A_P1][t], s_acc[A_P2][t]};
+    float aX[3] = {s_acc[A_X0][t], s_acc[A_X1][t], s_acc[A_X2][t]};
+    float G[3][3] = {{s_acc[A_G00][t], s_acc[A_G01][t], s_acc[A_G02][t]},
+                     {s_acc[A_G10][t], s_acc[A_G11][t], s_acc[A_G12][t]},
+                     {s_acc[A_G20][t], s_acc[A_G21][t], s_acc[A_G22][t]}};
+    finalize<float>(i, c, st.n, st, mat, g, star, solid_i, a2.w, aP, aX,
+                    s_acc[A_DU][t] - s_acc[A_DUC][t], s_acc[A_DD][t], G, p0.x, p0.z, p0.w, p1.x,
+                    a2.x, a2.y, a2.z, s.xs[i], s.ys[i], s.zs[i], out);
 }
 
 template <int LPI>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(kPB64)
 k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
              DevRates out, int cap)
 {
     (void)eos;
+    __shared__ double s_acc[A_N][kPB64];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / LPI) + grp;
-    const bool valid = i < n;
-    const int cnt = valid ? s.ncnt[i] : 0;
-    double4_32a a0 = make_double4_32a(0, 0, 0, 1), a1 = make_double4_32a(0, 0, 0, 0),
-            a2 = make_double4_32a(1, 1, 0, 0);
-    double sa[6] = {0, 0, 0, 0, 0, 0};
-    bool solid_i = false;
-    if (valid) {
-        a0 = s.rec64[i * 3 + 0];
-        a1 = s.rec64[i * 3 + 1];
-        a2 = s.rec64[i * 3 + 2];
-        solid_i = s.tys[i] == 1;
-        if (solid_i)
-            for (int k = 0; k < 6; ++k) sa[k] = s.sd264[i * 8 + k];
-    }
-    double aP[3] = {0, 0, 0}, aX[3] = {0, 0, 0}, du = 0.0, dD = 0.0;
-    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    const int32_t *list = s.nbr + i * (int64_t)cap;
-    for (int k = sub; k < cnt; k += LPI) {
-        const int j = list[k];
-        const double4_32a q0 = s.rec64[(int64_t)j * 3 + 0], q1 = s.rec64[(int64_t)j * 3 + 1];
-        const double4_32a q2 = s.rec64[(int64_t)j * 3 + 2];
-        const bool solid_j = s.tys[j] == 1;
-        double dx[3] = {a0.x - q0.x, a0.y - q0.y, a0.z - q0.z};
-        double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-        double r = sqrt(r2);
-        double hab = 0.5 * (a0.w + q0.w);
-        double gW = 0.0;
-        if (r > 0.0) {
-            double q = r / hab;
-            double sig = 1.0 / (kPi * hab * hab * hab);
-            double dW;
-            if (q < 1.0) dW = (sig / hab) * (-3.0 * q + 2.25 * q * q);
-            else {
-                double t = 2.0 - q;
-                dW = -(sig / hab) * 0.75 * t * t;
-            }
-            gW = dW / r;
-        }
-        double w = q1.x * gW;
-        double dv[3] = {a1.y - q1.y, a1.z - q1.z, a1.w - q1.w};
-        double vdx = dv[0] * dx[0] + dv[1] * dx[1] + dv[2] * dx[2];
-        double Pi = 0.0;
-        if (vdx < 0.0) {
-            double mu = hab * vdx / (r2 + mat.eta2 * hab * hab);
-            double cbar = 0.5 * (a2.w + q2.w);
-            double Dbar = 0.5 * (a2.x + q2.x);
-            Pi = (-mat.alpha_av * cbar * mu + mat.beta_av * mu * mu) / Dbar;
-        }
-        double fp = (a2.z + q2.z) * w, fv = Pi * w;
-        for (int d = 0; d < 3; ++d) {
-            aP[d] -= fp * dx[d];
-            aX[d] -= fv * dx[d];
-        }
-        double vw = vdx * w;
-        du += (a2.z + 0.5 * Pi) * vw;
-        dD += vw * q2.y;
-        if (solid_i || solid_j) {
-            double wd[3] = {w * dx[0], w * dx[1], w * dx[2]};
-            double sb[6] = {0, 0, 0, 0, 0, 0};
-            if (solid_j)
-                for (int kk = 0; kk < 6; ++kk) sb[kk] = s.sd264[(int64_t)j * 8 + kk];
-            double T[3][3] = {{sa[0] + sb[0], sa[3] + sb[3], sa[4] + sb[4]},
-                              {sa[3] + sb[3], sa[1] + sb[1], sa[5] + sb[5]},
-                              {sa[4] + sb[4], sa[5] + sb[5], sa[2] + sb[2]}};
-            for (int p = 0; p < 3; ++p) aX[p] += T[p][0] * wd[0] + T[p][1] * wd[1] + T[p][2] * wd[2];
+    const int64_t base = (int64_t)blockIdx.x * kPB64;
+#pragma unroll 1
+    for (int r = 0; r < LPI; ++r) {
+        const int slot = r * (kPB64 / LPI) + grp;
+        const int64_t i = base + slot;
+        const bool valid = i < n;
+        const int cnt = valid ? s.ncnt[i] : 0;
+        double4_32a a0 = make_double4_32a(0, 0, 0, 1), a1 = make_double4_32a(0, 0, 0, 0),
+                    a2 = make_double4_32a(1, 1, 0, 0);
+        double sa[6] = {0, 0, 0, 0, 0, 0};
+        bool solid_i = false;
+        if (valid) {
+            a0 = s.rec64[i * 3 + 0];
+            a1 = s.rec64[i * 3 + 1];
+            a2 = s.rec64[i * 3 + 2];
+            solid_i = s.tys[i] == 1;
             if (solid_i)
-                for (int p = 0; p < 3; ++p)
-                    for (int q = 0; q < 3; ++q) G[p][q] -= dv[p] * wd[q];
+                for (int k = 0; k < 6; ++k) sa[k] = s.sd264[i * 8 + k];
+        }
+        double aP[3] = {0, 0, 0}, aX[3] = {0, 0, 0}, du = 0.0, dD = 0.0;
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const int32_t *list = s.nbr + i * (int64_t)cap;
+        for (int k = sub; k < cnt; k += LPI) {
+            const int j = list[k];
+            const double4_32a q0 = s.rec64[(int64_t)j * 3 + 0], q1 = s.rec64[(int64_t)j * 3 + 1];
+            const double4_32a q2 = s.rec64[(int64_t)j * 3 + 2];
+            const bool solid_j = s.tys[j] == 1;
+            double dx[3] = {a0.x - q0.x, a0.y - q0.y, a0.z - q0.z};
+            double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+            double r = sqrt(r2);
+            double hab = 0.5 * (a0.w + q0.w);
+            double gW = 0.0;
+            if (r > 0.0) {
+                double q = r / hab;
+                double sig = 1.0 / (kPi * hab * hab * hab);
+                double dW;
+                if (q < 1.0) dW = (sig / hab) * (-3.0 * q + 2.25 * q * q);
+                else {
+                    double tq = 2.0 - q;
+                    dW = -(sig / hab) * 0.75 * tq * tq;
+                }
+                gW = dW / r;
+            }
+            double w = q1.x * gW;
+            double dv[3] = {a1.y - q1.y, a1.z - q1.z, a1.w - q1.w};
+            double vdx = dv[0] * dx[0] + dv[1] * dx[1] + dv[2] * dx[2];
+            double Pi = 0.0;
+            if (vdx < 0.0) {
+                double mu = hab * vdx / (r2 + mat.eta2 * hab * hab);
+                double cbar = 0.5 * (a2.w + q2.w);
+                double Dbar = 0.5 * (a2.x + q2.x);
+                Pi = (-mat.alpha_av * cbar * mu + mat.beta_av * mu * mu) / Dbar;
+            }
+            double fp = (a2.z + q2.z) * w, fv = Pi * w;
+            for (int d = 0; d < 3; ++d) {
+                aP[d] -= fp * dx[d];
+                aX[d] -= fv * dx[d];
+            }
+            double vw = vdx * w;
+            du += (a2.z + 0.5 * Pi) * vw;
+            dD += vw * q2.y;
+            if (solid_i || solid_j) {
+                double wd[3] = {w * dx[0], w * dx[1], w * dx[2]};
+                double sb[6] = {0, 0, 0, 0, 0, 0};
+                if (solid_j)
+                    for (int kk = 0; kk < 6; ++kk) sb[kk] = s.sd264[(int64_t)j * 8 + kk];
+                double T[3][3] = {{sa[0] + sb[0], sa[3] + sb[3], sa[4] + sb[4]},
+                                  {sa[3] + sb[3], sa[1] + sb[1], sa[5] + sb[5]},
+                                  {sa[4] + sb[4], sa[5] + sb[5], sa[2] + sb[2]}};
+                for (int pp = 0; pp < 3; ++pp)
+                    aX[pp] += T[pp][0] * wd[0] + T[pp][1] * wd[1] + T[pp][2] * wd[2];
+                if (solid_i)
+                    for (int pp = 0; pp < 3; ++pp)
+                        for (int qq = 0; qq < 3; ++qq) G[pp][qq] -= dv[pp] * wd[qq];
+            }
+        }
+        double acc[A_N] = {aP[0], aP[1], aP[2], aX[0], aX[1], aX[2], du, 0.0, dD,
+                           G[0][0], G[0][1], G[0][2], G[1][0], G[1][1], G[1][2],
+                           G[2][0], G[2][1], G[2][2]};
+#pragma unroll
+        for (int a = 0; a < A_N; ++a) {
+            double v = acc[a];
+            for (int o = LPI / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (sub == 0) s_acc[a][slot] = v;
         }
     }
-    for (int o = LPI / 2; o > 0; o >>= 1) {
-        for (int d = 0; d < 3; ++d) {
-            aP[d] += __shfl_xor_sync(0xffffffffu, aP[d], o);
-            aX[d] += __shfl_xor_sync(0xffffffffu, aX[d], o);
-        }
-        du += __shfl_xor_sync(0xffffffffu, du, o);
-        dD += __shfl_xor_sync(0xffffffffu, dD, o);
-        for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q) G[p][q] += __shfl_xor_sync(0xffffffffu, G[p][q], o);
-    }
-    if (!valid || sub != 0) return;
+    __syncthreads();
+    const int64_t i = base + threadIdx.x;
+    if (i >= n) return;
+    const int t = threadIdx.x;
     const int c = s.perm[i];
     const int star = st.star ? st.star[c] : 0;
+    const double4_32a a0 = s.rec64[i * 3 + 0], a1 = s.rec64[i * 3 + 1], a2 = s.rec64[i * 3 + 2];
     const double *pp = s.pp64 + i * 8;
-    finalize<double>(i, c, st.n, st, mat, g, star, solid_i, a2.x, aP, aX, du, dD, G, pp[0],
-                     pp[2], pp[3], pp[4], a1.y, a1.z, a1.w, a0.x, a0.y, a0.z, out);
+    const bool solid_i = s.tys[i] == 1;
+    double aP[3] = {s_acc[A_P0][t], s_acc[A_P1][t], s_acc[A_P2][t]};
+    double aX[3] = {s_acc[A_X0][t], s_acc[A_X1][t], s_acc[A_X2][t]};
+    double G[3][3] = {{s_acc[A_G00][t], s_acc[A_G01][t], s_acc[A_G02][t]},
+                      {s_acc[A_G10][t], s_acc[A_G11][t], s_acc[A_G12][t]},
+                      {s_acc[A_G20][t], s_acc[A_G21][t], s_acc[A_G22][t]}};
+    finalize<double>(i, c, st.n, st, mat, g, star, solid_i, a2.x, aP, aX, s_acc[A_DU][t],
+                     s_acc[A_DD][t], G, pp[0], pp[2], pp[3], pp[4], a1.y, a1.z, a1.w, a0.x,
+                     a0.y, a0.z, out);
 }
 
 }  // namespace
@@ -543,24 +610,15 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
 void launch_density(const DevState &st, const Scratch &s, const DevEos &eos, const DevMetric &g,
                     const DevRates &out, int cap, int lanes, int fp64, cudaStream_t stream)
 {
-    const int T = 128;
     int64_t n = st.n;
     if (fp64) {
-        if (lanes == 4) {
-            k_density_fp64<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos, g,
-                                                                                 out, cap);
-        } else {
-            k_density_fp64<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos, g,
-                                                                                 out, cap);
-        }
+        int nb = (int)((n + kPB64 - 1) / kPB64);
+        if (lanes == 4) k_density_fp64<4><<<nb, kPB64, 0, stream>>>(n, st, s, eos, g, out, cap);
+        else k_density_fp64<8><<<nb, kPB64, 0, stream>>>(n, st, s, eos, g, out, cap);
     } else {
-        if (lanes == 4) {
-            k_density_mixed<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos,
-                                                                                  g, out, cap);
-        } else {
-            k_density_mixed<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos,
-                                                                                  g, out, cap);
-        }
+        int nb = (int)((n + kPB - 1) / kPB);
+        if (lanes == 4) k_density_mixed<4><<<nb, kPB, 0, stream>>>(n, st, s, eos, g, out, cap);
+        else k_density_mixed<8><<<nb, kPB, 0, stream>>>(n, st, s, eos, g, out, cap);
     }
 }
 
@@ -570,23 +628,13 @@ void launch_force(const DevState &st, const Scratch &s, const DevEos &eos, const
 {
     int64_t n = st.n;
     if (fp64) {
-        const int T = 64;
-        if (lanes == 4) {
-            k_force_fp64<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos, mat,
-                                                                               g, out, cap);
-        } else {
-            k_force_fp64<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos, mat,
-                                                                               g, out, cap);
-        }
+        int nb = (int)((n + kPB64 - 1) / kPB64);
+        if (lanes == 4) k_force_fp64<4><<<nb, kPB64, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
+        else k_force_fp64<8><<<nb, kPB64, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
     } else {
-        const int T = 128;
-        if (lanes == 4) {
-            k_force_mixed<4><<<(int)((n + T / 4 - 1) / (T / 4)), T, 0, stream>>>(n, st, s, eos, mat,
-                                                                                g, out, cap);
-        } else {
-            k_force_mixed<8><<<(int)((n + T / 8 - 1) / (T / 8)), T, 0, stream>>>(n, st, s, eos, mat,
-                                                                                g, out, cap);
-        }
+        int nb = (int)((n + kPB - 1) / kPB);
+        if (lanes == 4) k_force_mixed<4><<<nb, kPB, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
+        else k_force_mixed<8><<<nb, kPB, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
     }
 }
 

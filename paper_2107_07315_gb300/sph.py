@@ -260,7 +260,7 @@ def sph_timing(ctx: SphCtx, enable: bool) -> None:
 
 
 def sph_timing_read(ctx: SphCtx) -> np.ndarray:
-    out = np.zeros(8, np.float64)
+    out = np.zeros(12, np.float64)
     _check(lib().sph_timing_read(ctx.handle, out.ctypes.data_as(_d)), "sph_timing_read")
     return out
 
