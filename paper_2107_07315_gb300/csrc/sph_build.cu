@@ -436,8 +436,10 @@ constexpr int kStackCap = (kBranch - 1) * 10 + 2;      // depth bound for <= 10 
 // 5 u r^2 + 7 u hs^2 for r <= 2 hs; the band M = c1 hs + 3.2e-6 hs^2 with
 // c1 = 1.67e-6 X is twice that bound.  Inside the band the pair is decided
 // by the FP64 predicate.
+// At most 64 registers (16 blocks of 2 warps per SM): the walk is latency
+// bound and gains more from resident warps than from extra registers.
 template <bool MULTI_STAR>
-__global__ void __launch_bounds__(kListThreads)
+__global__ void __launch_bounds__(kListThreads, 16)
 k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, const double *zs,
             const double *hs, const int32_t *leaf_start, const int32_t *leaf_star,
             const int32_t *leaf_of, TreeLevels tl, const float4 *nodes, int cap, int32_t *nbr,

@@ -122,26 +122,28 @@ __device__ __forceinline__ Prep<T> eos_prep(const DevEos &eos, const DevMetric &
     return p;
 }
 
-// Block layout shared by the pair kernels: a block owns kPB consecutive
-// sorted particles.  Phase 1 runs the pair sums: LPI threads share one
-// particle's list, kPB/LPI particles per round, LPI rounds; the group's sums
-// are combined with xor shuffles (fixed order) and parked in shared memory.
-// Phase 2 gives every thread one particle for the per-particle work (EoS,
-// finalize) at full SIMD width.
-constexpr int kPB = 128;    // particles (and threads) per block, mixed precision
-constexpr int kPB64 = 64;   // particles (and threads) per block, FP64
+// Block layout shared by the pair kernels: a block owns PB = (threads/LPI)*R
+// consecutive sorted particles.  Phase 1 runs the pair sums: LPI threads
+// share one particle's list, threads/LPI particles per round, R rounds; the
+// group's sums are combined with xor shuffles (fixed order) and parked in
+// shared memory.  Phase 2 gives each of the first PB threads one particle
+// for the per-particle work (EoS, finalize).
+constexpr int kTB = 128;    // threads per block, mixed precision
+constexpr int kTB64 = 64;   // threads per block, FP64
+constexpr int kRounds = 4;  // phase-1 rounds per block
 
 // ------------------------------------------------------------------ density
-template <int LPI>
-__global__ void __launch_bounds__(kPB)
+template <int LPI, int R>
+__global__ void __launch_bounds__(kTB)
 k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRates out, int cap)
 {
-    __shared__ float s_D[kPB];
+    constexpr int PB = kTB / LPI * R;  // particles per block
+    __shared__ float s_D[PB];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t base = (int64_t)blockIdx.x * kPB;
+    const int64_t base = (int64_t)blockIdx.x * PB;
 #pragma unroll 1
-    for (int r = 0; r < LPI; ++r) {
-        const int slot = r * (kPB / LPI) + grp;
+    for (int r = 0; r < R; ++r) {
+        const int slot = r * (kTB / LPI) + grp;
         const int64_t i = base + slot;
         const bool valid = i < n;
         const int cnt = valid ? s.ncnt[i] : 0;
@@ -182,7 +184,7 @@ k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevR
     }
     __syncthreads();
     const int64_t i = base + threadIdx.x;
-    if (i >= n) return;
+    if (threadIdx.x >= PB || i >= n) return;
     const float D = s_D[threadIdx.x];
     const int c = s.perm[i];
     const int star = st.star ? st.star[c] : 0;
@@ -212,16 +214,17 @@ k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevR
     out.ncount[c] = s.ncnt[i];
 }
 
-template <int LPI>
-__global__ void __launch_bounds__(kPB64)
+template <int LPI, int R>
+__global__ void __launch_bounds__(kTB64)
 k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRates out, int cap)
 {
-    __shared__ double s_D[kPB64];
+    constexpr int PB = kTB64 / LPI * R;
+    __shared__ double s_D[PB];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t base = (int64_t)blockIdx.x * kPB64;
+    const int64_t base = (int64_t)blockIdx.x * PB;
 #pragma unroll 1
-    for (int r = 0; r < LPI; ++r) {
-        const int slot = r * (kPB64 / LPI) + grp;
+    for (int r = 0; r < R; ++r) {
+        const int slot = r * (kTB64 / LPI) + grp;
         const int64_t i = base + slot;
         const bool valid = i < n;
         const int cnt = valid ? s.ncnt[i] : 0;
@@ -258,7 +261,7 @@ k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRa
     }
     __syncthreads();
     const int64_t i = base + threadIdx.x;
-    if (i >= n) return;
+    if (threadIdx.x >= PB || i >= n) return;
     const double D = s_D[threadIdx.x];
     const double4_32a a0 = s.rec64[i * 3 + 0];
     const double mi = s.rec64[i * 3 + 1].x;
@@ -365,20 +368,21 @@ __device__ __forceinline__ void finalize(int64_t i, int c, int64_t N, const DevS
 enum { A_P0, A_P1, A_P2, A_X0, A_X1, A_X2, A_DU, A_DUC, A_DD, A_G00, A_G01, A_G02, A_G10, A_G11,
        A_G12, A_G20, A_G21, A_G22, A_N };
 
-template <int LPI>
-__global__ void __launch_bounds__(kPB)
+template <int LPI, int R>
+__global__ void __launch_bounds__(kTB)
 k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
               DevRates out, int cap)
 {
     (void)eos;
-    __shared__ float s_acc[A_N][kPB];
+    constexpr int PB = kTB / LPI * R;
+    __shared__ float s_acc[A_N][PB];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t base = (int64_t)blockIdx.x * kPB;
+    const int64_t base = (int64_t)blockIdx.x * PB;
     const float alpha_av = (float)mat.alpha_av, beta_av = (float)mat.beta_av;
     const float eta2 = (float)mat.eta2;
 #pragma unroll 1
-    for (int r = 0; r < LPI; ++r) {
-        const int slot = r * (kPB / LPI) + grp;
+    for (int r = 0; r < R; ++r) {
+        const int slot = r * (kTB / LPI) + grp;
         const int64_t i = base + slot;
         const bool valid = i < n;
         const int cnt = valid ? s.ncnt[i] : 0;
@@ -475,7 +479,7 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
     }
     __syncthreads();
     const int64_t i = base + threadIdx.x;
-    if (i >= n) return;
+    if (threadIdx.x >= PB || i >= n) return;
     const int t = threadIdx.x;
     const int c = s.perm[i];
     const int star = st.star ? st.star[c] : 0;
@@ -492,18 +496,19 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
                     a2.x, a2.y, a2.z, s.xs[i], s.ys[i], s.zs[i], out);
 }
 
-template <int LPI>
-__global__ void __launch_bounds__(kPB64)
+template <int LPI, int R>
+__global__ void __launch_bounds__(kTB64)
 k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
              DevRates out, int cap)
 {
     (void)eos;
-    __shared__ double s_acc[A_N][kPB64];
+    constexpr int PB = kTB64 / LPI * R;
+    __shared__ double s_acc[A_N][PB];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t base = (int64_t)blockIdx.x * kPB64;
+    const int64_t base = (int64_t)blockIdx.x * PB;
 #pragma unroll 1
-    for (int r = 0; r < LPI; ++r) {
-        const int slot = r * (kPB64 / LPI) + grp;
+    for (int r = 0; r < R; ++r) {
+        const int slot = r * (kTB64 / LPI) + grp;
         const int64_t i = base + slot;
         const bool valid = i < n;
         const int cnt = valid ? s.ncnt[i] : 0;
@@ -588,7 +593,7 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
     }
     __syncthreads();
     const int64_t i = base + threadIdx.x;
-    if (i >= n) return;
+    if (threadIdx.x >= PB || i >= n) return;
     const int t = threadIdx.x;
     const int c = s.perm[i];
     const int star = st.star ? st.star[c] : 0;
@@ -607,18 +612,30 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
 
 }  // namespace
 
+// Particles per block of each kernel variant (threads / lanes * rounds).
+template <int LPI>
+constexpr int pb_mixed() { return kTB / LPI * kRounds; }
+template <int LPI>
+constexpr int pb_fp64() { return kTB64 / LPI * kRounds; }
+
 void launch_density(const DevState &st, const Scratch &s, const DevEos &eos, const DevMetric &g,
                     const DevRates &out, int cap, int lanes, int fp64, cudaStream_t stream)
 {
     int64_t n = st.n;
     if (fp64) {
-        int nb = (int)((n + kPB64 - 1) / kPB64);
-        if (lanes == 4) k_density_fp64<4><<<nb, kPB64, 0, stream>>>(n, st, s, eos, g, out, cap);
-        else k_density_fp64<8><<<nb, kPB64, 0, stream>>>(n, st, s, eos, g, out, cap);
+        if (lanes == 4)
+            k_density_fp64<4, kRounds><<<(int)((n + pb_fp64<4>() - 1) / pb_fp64<4>()), kTB64, 0,
+                                         stream>>>(n, st, s, eos, g, out, cap);
+        else
+            k_density_fp64<8, kRounds><<<(int)((n + pb_fp64<8>() - 1) / pb_fp64<8>()), kTB64, 0,
+                                         stream>>>(n, st, s, eos, g, out, cap);
     } else {
-        int nb = (int)((n + kPB - 1) / kPB);
-        if (lanes == 4) k_density_mixed<4><<<nb, kPB, 0, stream>>>(n, st, s, eos, g, out, cap);
-        else k_density_mixed<8><<<nb, kPB, 0, stream>>>(n, st, s, eos, g, out, cap);
+        if (lanes == 4)
+            k_density_mixed<4, kRounds><<<(int)((n + pb_mixed<4>() - 1) / pb_mixed<4>()), kTB, 0,
+                                          stream>>>(n, st, s, eos, g, out, cap);
+        else
+            k_density_mixed<8, kRounds><<<(int)((n + pb_mixed<8>() - 1) / pb_mixed<8>()), kTB, 0,
+                                          stream>>>(n, st, s, eos, g, out, cap);
     }
 }
 
@@ -628,13 +645,19 @@ void launch_force(const DevState &st, const Scratch &s, const DevEos &eos, const
 {
     int64_t n = st.n;
     if (fp64) {
-        int nb = (int)((n + kPB64 - 1) / kPB64);
-        if (lanes == 4) k_force_fp64<4><<<nb, kPB64, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
-        else k_force_fp64<8><<<nb, kPB64, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
+        if (lanes == 4)
+            k_force_fp64<4, kRounds><<<(int)((n + pb_fp64<4>() - 1) / pb_fp64<4>()), kTB64, 0,
+                                       stream>>>(n, st, s, eos, mat, g, out, cap);
+        else
+            k_force_fp64<8, kRounds><<<(int)((n + pb_fp64<8>() - 1) / pb_fp64<8>()), kTB64, 0,
+                                       stream>>>(n, st, s, eos, mat, g, out, cap);
     } else {
-        int nb = (int)((n + kPB - 1) / kPB);
-        if (lanes == 4) k_force_mixed<4><<<nb, kPB, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
-        else k_force_mixed<8><<<nb, kPB, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
+        if (lanes == 4)
+            k_force_mixed<4, kRounds><<<(int)((n + pb_mixed<4>() - 1) / pb_mixed<4>()), kTB, 0,
+                                        stream>>>(n, st, s, eos, mat, g, out, cap);
+        else
+            k_force_mixed<8, kRounds><<<(int)((n + pb_mixed<8>() - 1) / pb_mixed<8>()), kTB, 0,
+                                        stream>>>(n, st, s, eos, mat, g, out, cap);
     }
 }
 
