@@ -81,19 +81,83 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+class _Nvml:
+    """Minimal ctypes view of NVML (clock and clock-event-reason queries only)."""
+
+    SM = 1  # NVML_CLOCK_SM
+    REASONS = ((0x8, "hw_slowdown"), (0x40, "hw_thermal_slowdown"),
+               (0x20, "sw_thermal_slowdown"), (0x4, "sw_power_cap"),
+               (0x80, "hw_power_brake_slowdown"))
+
+    def __init__(self, uuid: str | None, index: int):
+        import ctypes as C
+
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = C.c_void_p()
+        ok = False
+        if uuid:
+            ok = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), C.byref(self.h)) == 0
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(index, C.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = C.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, C.byref(v))
+        self.max_mhz = float(v.value)
+
+    def sample(self):
+        C = self.C
+        mhz, bits = C.c_uint(), C.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, C.byref(mhz)) != 0:
+            return None
+        self.reasons_fn(self.h, C.byref(bits))
+        return float(mhz.value), int(bits.value)
+
+
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region.
+
+    NVML is polled every 0.5 ms from a thread (the timed region of a short run
+    lasts only milliseconds); without NVML, nvidia-smi is polled every 200 ms.
+    """
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, uuid: str | None = None):
         self.proc = None
+        self.thread = None
         self.gpu = gpu_index
+        self.uuid = uuid
         self.out = os.path.join("/tmp", "sph_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+        try:
+            self.nvml = _Nvml(uuid, gpu_index)
+        except Exception:
+            self.nvml = None
 
     def start(self):
+        import threading
+
+        self.samples = []
+        if self.nvml is not None:
+            self.stop_flag = threading.Event()
+
+            def poll():
+                while not self.stop_flag.is_set():
+                    s = self.nvml.sample()
+                    if s is not None:
+                        self.samples.append(s)
+                    time.sleep(0.0005)
+
+            self.thread = threading.Thread(target=poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.f = open(self.out, "w")
             self.proc = subprocess.Popen(
@@ -104,6 +168,22 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join()
+            s = self.nvml.sample()
+            if s is not None:
+                self.samples.append(s)
+            if not self.samples:
+                return None
+            reasons = set()
+            for _, bits in self.samples:
+                for b, nm in _Nvml.REASONS:
+                    if bits & b:
+                        reasons.add(nm)
+            return {"sm_mhz": statistics.median(m for m, _ in self.samples),
+                    "sm_max_mhz": self.nvml.max_mhz, "reasons": sorted(reasons),
+                    "samples": len(self.samples), "source": "nvml, 0.5 ms period"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -129,7 +209,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms period"}
 
 
 PROFILE_FILES = {
@@ -200,26 +280,22 @@ def run_ours(args):
         sph.sph_sync(ctx)
     sph.sph_timing_read(ctx)  # discard warm-up samples
     stats0 = sph.sph_stats(ctx)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    clk = ClockSampler(torch.cuda.current_device())
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    clk = ClockSampler(torch.cuda.current_device(), uuid)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(float(k))  # evict L2 between timed steps (outside the events)
-            evs[k][0].record(stream)
-            sph.sph_step(ctx, dt, 1)
-            evs[k][1].record(stream)
-    torch.cuda.synchronize()
+    t_ms, _ = time_steps(ctx, dt, args.steps, 0, flush, stream)
     if ws > 1:
         dist.barrier()
     clocks = clk.stop()
     sph.sph_sync(ctx)
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ms = float(sum(step_ms))
     tim = sph.sph_timing_read(ctx)
     stats1 = sph.sph_stats(ctx)
     pairs = float(stats1[1] - stats0[1])
@@ -305,8 +381,33 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)},
         "clocks": clocks,
     }
+    if ws == 1 and args.fp64_steps > 0 and prec == sph.SPH_MIXED:
+        # the plain FP64 GPU path on the same star, same step and flush protocol
+        d64 = sph.device_state(st, dev)
+        torch.cuda.synchronize()
+        c64 = sph.sph_init(d64, eos, I.DEFAULT_MATERIAL, met, sph.SPH_FP64,
+                           dict(h_nmin=55, h_nmax=65, use_graph=1), stream=stream.cuda_stream)
+        t64, p64 = time_steps(c64, dt, args.fp64_steps, 3, flush, stream)
+        sph.sph_free(c64)
+        del d64
+        v64 = p64 / (t64 * 1e-3)
+        out["fp64"] = {"value": v64, "unit": "pairs/s", "ms_per_step": t64 / args.fp64_steps,
+                       "steps": args.fp64_steps, "mixed_speedup": value / v64}
     if not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline(st, eos, met, args.cpu_sample)
+        cb, ids, ro = cpu_baseline(st, eos, met, args.cpu_sample)
+        out["cpu_baseline"] = cb
+        if args.workload == "star":
+            # per-field error of one right-hand side of the initial state against
+            # the oracle on the sampled particles (normalised as in the tests)
+            par = {"mixed": parity_errors(gpu_rates_at(st, eos, met, sph.SPH_MIXED, dev, stream),
+                                          ro, ids)}
+            if args.fp64_steps > 0:
+                par["fp64"] = parity_errors(gpu_rates_at(st, eos, met, sph.SPH_FP64, dev, stream),
+                                            ro, ids)
+            par["tolerance"] = {"fp64": 1e-12, "mixed": {"D": 1e-5, "rho": 1e-5, "a": 1e-5,
+                                                          "dudt": 1e-5, "drhodt": 1e-5,
+                                                          "deps": 1e-4, "dS": 1e-4}}
+            out["parity"] = par
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -366,27 +467,108 @@ def rooflines(tim, n, pairs_step, solid_pairs, mixed):
 
 
 def oracle_sample_rhs(st, eos, met, sample: int, seed: int):
+    """Oracle rates of `sample` random particles (brute force over all)."""
     import oracle
     from paper_2107_07315_gb300 import inputs as I
 
     rng = np.random.default_rng(seed)
     ids = np.sort(rng.choice(len(st["x"]), size=sample, replace=False)).astype(np.int64)
     t0 = time.perf_counter()
-    r = oracle.rhs(st, eos, I.DEFAULT_MATERIAL, met, subset=ids)
+    r = oracle.rhs(st, eos, I.DEFAULT_MATERIAL, met, subset=ids, scales=True)
     t1 = time.perf_counter()
     pairs = float(r["ncount"][ids].sum())
-    return pairs, t1 - t0
+    return pairs, t1 - t0, ids, r
+
+
+def auto_sample(st, eos, met, target_s: float) -> int:
+    """Particle sample whose oracle right-hand side takes about target_s."""
+    oracle_sample_rhs(st, eos, met, min(200, len(st["x"])), 2)  # thread start-up
+    cal = min(4000, len(st["x"]))
+    _, sec, _, _ = oracle_sample_rhs(st, eos, met, cal, 3)
+    return int(min(len(st["x"]), max(cal, cal * target_s / max(sec, 1e-3))))
 
 
 def cpu_baseline(st, eos, met, sample: int):
     import oracle
 
-    pairs, sec = oracle_sample_rhs(st, eos, met, sample, 7)
+    if sample <= 0:
+        sample = auto_sample(st, eos, met, 15.0)
+    pairs, sec, ids, r = oracle_sample_rhs(st, eos, met, sample, 7)
     return {"value": pairs / sec, "unit": "pairs/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": "right-hand side of %d random particles of the %d-particle star "
                       "(brute-force O(N^2) neighbour search over all particles, FP64), "
-                      "%.1f s" % (sample, len(st["x"]), sec)}
+                      "%.1f s" % (sample, len(st["x"]), sec)}, ids, r
+
+
+def parity_errors(g, o, ids):
+    """Max normalised error per field on the sampled particles:
+    |q_gpu - q_oracle| / max(|q_oracle|, absolute-summand scale of q)."""
+    sc = o["scale"]
+
+    def err(qg, qo, s):
+        d = np.abs(qg - qo)
+        den = np.maximum(np.abs(qo), s)
+        return float(np.max(np.where(den > 0, d / np.where(den > 0, den, 1.0),
+                                     np.where(d == 0, 0.0, np.inf)))) if len(d) else 0.0
+
+    e = {"D": err(g["D"][ids], o["D"][ids], sc["D"][ids]),
+         "rho": err(g["rho"][ids], o["rho"][ids], 0.0),
+         "a": max(err(g[k][ids], o[k][ids], sc["a"][ids]) for k in ("ax", "ay", "az")),
+         "dudt": err(g["dudt"][ids], o["dudt"][ids], sc["du"][ids]),
+         "drhodt": err(g["drhodt"][ids], o["drhodt"][ids], sc["drho"][ids])}
+    sid = ids[sc["dS"][ids] > 0]
+    if len(sid):
+        e["deps"] = max(err(g["deps"][c][sid], o["deps"][c][sid], sc["eps"][sid]) for c in range(6))
+        e["dS"] = max(err(g["dS"][c][sid], o["dS"][c][sid], sc["dS"][sid]) for c in range(6))
+    e["neighbour_counts_equal"] = bool(np.array_equal(g["ncount"][ids], o["ncount"][ids]))
+    e["particles"] = int(len(ids))
+    e["solid_particles"] = int(len(sid))
+    return e
+
+
+def gpu_rates_at(st, eos, met, prec, dev, stream):
+    """One right-hand side of the initial state through the C ABI (host copy)."""
+    import torch
+
+    from paper_2107_07315_gb300 import inputs as I
+    from paper_2107_07315_gb300 import sph
+
+    d = sph.device_state(st, dev)
+    torch.cuda.synchronize()
+    ctx = sph.sph_init(d, eos, I.DEFAULT_MATERIAL, met, prec, dict(h_nmin=55, h_nmax=65),
+                       stream=stream.cuda_stream)
+    rates = sph.alloc_rates(len(st["x"]), dev)
+    torch.cuda.synchronize()
+    sph.sph_rhs(ctx, rates)
+    sph.sph_sync(ctx)
+    out = sph.to_numpy(rates)
+    sph.sph_free(ctx)
+    return out
+
+
+def time_steps(ctx, dt, steps, warmup, flush, stream):
+    """Per-step CUDA-event time (ms) of `steps` KDK steps after `warmup`."""
+    import torch
+
+    from paper_2107_07315_gb300 import sph
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            sph.sph_step(ctx, dt, 1)
+    sph.sph_sync(ctx)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    p0 = sph.sph_stats(ctx)[1]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            sph.sph_step(ctx, dt, 1)
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return float(sum(a.elapsed_time(b) for a, b in evs)), float(sph.sph_stats(ctx)[1] - p0)
 
 
 def run_reference(args):
@@ -396,11 +578,16 @@ def run_reference(args):
     import oracle
 
     st, eos, met, _ = make_star(1, args.n)
+    sample = args.cpu_sample
+    if sample <= 0:
+        # per step a bounded sample: the whole run stays within a few minutes
+        per_step = min(20.0, 150.0 / max(args.steps, 1))
+        sample = auto_sample(st, eos, met, per_step)
     for k in range(args.warmup):
-        oracle_sample_rhs(st, eos, met, max(args.cpu_sample // 8, 16), 100 + k)
+        oracle_sample_rhs(st, eos, met, max(sample // 16, 16), 100 + k)
     tot_p, tot_s = 0.0, 0.0
     for k in range(args.steps):
-        p, s = oracle_sample_rhs(st, eos, met, args.cpu_sample, 200 + k)
+        p, s, _, _ = oracle_sample_rhs(st, eos, met, sample, 200 + k)
         tot_p += p
         tot_s += s
     v = tot_p / tot_s
@@ -414,7 +601,7 @@ def run_reference(args):
            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": oracle.num_threads(),
                             "kind": "oracle",
                             "sample": "%d random particles per step, brute-force neighbours"
-                                      % args.cpu_sample},
+                                      % sample},
            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -432,7 +619,10 @@ def main():
     ap.add_argument("--workload", choices=("star", "ensemble"), default="star")
     ap.add_argument("--nstars", type=int, default=64)
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--cpu-sample", type=int, default=8000)
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="oracle particle sample; 0 sizes it to about 15 s of host time")
+    ap.add_argument("--fp64-steps", type=int, default=5,
+                    help="timed steps of the plain FP64 path on the same star (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count-solid", type=int, default=1)
     args = ap.parse_args()
