@@ -312,9 +312,10 @@ __device__ __forceinline__ float4 node_merge_a(float4 a, float4 b)
 __device__ __forceinline__ float4 node_merge_b(float4 a, float4 b)
 {
     int sa = __float_as_int(a.w), sb = __float_as_int(b.w);
-    int lo = min(sa & 0xffff, sb & 0xffff), hi = max(sa >> 16, sb >> 16);
+    int lo = min(sa & 0xffff, sb & 0xffff);
+    int hi = max((int)((unsigned)sa >> 16), (int)((unsigned)sb >> 16));
     return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z),
-                       __int_as_float(lo | (hi << 16)));
+                       __int_as_float((int)((unsigned)lo | ((unsigned)hi << 16))));
 }
 
 // Leaf boxes and the implicit 8-ary tree above them.  Boxes are rounded
@@ -342,7 +343,7 @@ __global__ void k_tree(const double *xs, const double *ys, const double *zs, con
         a = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]),
                         __double2float_rd(lo[2]), __double2float_ru(hm));
         b = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]),
-                        __double2float_ru(hi[2]), __int_as_float(s | (s << 16)));
+                        __double2float_ru(hi[2]), __int_as_float((int)((unsigned)s | ((unsigned)s << 16))));
         nodes[2 * ((int64_t)tl.offset[0] + l) + 0] = a;
         nodes[2 * ((int64_t)tl.offset[0] + l) + 1] = b;
     }
@@ -419,17 +420,25 @@ __device__ __forceinline__ bool pair_in_fp64(double xa, double ya, double za, do
 
 constexpr int kListThreads = 64;
 constexpr int kListWarps = kListThreads / 32;
+constexpr int kGroup = 8;                              // particles per warp
+constexpr int kSub = 32 / kGroup;                      // lanes per particle
 constexpr int kCandCap = 160;                          // candidate leaves buffered per warp
 constexpr int kStackCap = (kBranch - 1) * 10 + 2;      // depth bound for <= 10 levels
 
-// One warp per 32 consecutive sorted particles.  Phase 1 walks the implicit
-// 8-ary tree depth first with a warp-uniform stack: the 8 children of a node
-// are tested together (one ballot each: bit l set when the child box lies
-// within h_l + h_max(child) of lane l's particle), surviving inner children
-// are pushed in reverse order, surviving leaves are buffered in shared
-// memory with their ballot.  Phase 2: every lane screens the particles of the
-// buffered leaves whose ballot has its bit, in buffer order (ascending leaf,
-// hence ascending sorted index).
+// One warp per 8 consecutive sorted particles, four lanes per particle:
+// lane = 8 s + q serves particle q as its sub-lane s.
+//
+// Phase 1 walks the implicit 8-ary tree depth first with a warp-uniform
+// stack in shared memory.  The 8 children of a popped node are tested in two
+// rounds, sub-lane s taking child 4r + s against its particle (box distance
+// below h_q + h_max(child)); the two ballots give every child an 8-bit mask
+// of the particles it may hold neighbours of.  Children hit by some particle
+// are pushed in reverse order (inner nodes) or appended with their mask to a
+// shared leaf buffer (leaves), so the buffer stays in ascending leaf order.
+// Phase 2: the four sub-lanes of particle q step together through the
+// buffered leaves whose mask has bit q; sub-lane s screens the leaf's
+// particles s and s + 4.  Two ballots give the particle's 8-bit hit mask, so
+// each hit is written at its rank: lists are in ascending sorted index.
 //
 // Screening uses FP32 positions (pos4 = fl32(x, y, z, h)).  With u = 2^-24
 // and X = max |x|, |fl32 error of r^2 - (h_a+h_b)^2| <= 4 sqrt(3) u X r +
@@ -446,24 +455,28 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             int32_t *ncnt, DevScalars *sc)
 {
     __shared__ int s_leaf[kListWarps][kCandCap];
-    __shared__ unsigned s_mask[kListWarps][kCandCap];
+    __shared__ unsigned char s_mask[kListWarps][kCandCap];
+    __shared__ unsigned s_stack[kListWarps][kStackCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane & (kGroup - 1), sub = lane / kGroup;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const float c1 = sc->screen_c1;
     const float eps = (float)sc->eps_abs;
-    const int64_t ngroups = (n + 31) / 32;
+    const int64_t ngroups = (n + kGroup - 1) / kGroup;
+    unsigned *stack = s_stack[warp];
     unsigned long long nre = 0, pairs = 0;
     bool over = false;
-    // Persistent warps: each claims the next group of 32 sorted particles
-    // from a counter (reset at the start of every right-hand side), which
-    // evens out the uneven cost of groups across the SMs.
+    // Persistent warps: each claims the next group of sorted particles from a
+    // counter (reset at the start of every right-hand side), which evens out
+    // the uneven cost of groups across the SMs.
     while (true) {
     int64_t grp = 0;
     if (lane == 0) grp = (int64_t)atomicAdd(&sc->list_next, 1u);
     grp = __shfl_sync(0xffffffffu, grp, 0);
     if (grp >= ngroups) break;
-    const int64_t i = grp * 32 + lane;
+    const int64_t i = grp * kGroup + q;
     const bool valid = i < n;
-    int cnt = 0;
+    int cnt = 0;  // equal on the four sub-lanes of a particle
     // invalid lanes sit far away: every box and pair test fails for them
     float4 p = make_float4(3e38f, 3e38f, 3e38f, 0.f);
     int star = 0;
@@ -481,100 +494,120 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
         bool h = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
         if (MULTI_STAR) {
             int sr = __float_as_int(b.w);
-            h = h && star >= (sr & 0xffff) && star <= (sr >> 16);
+            h = h && star >= (sr & 0xffff) && star <= (int)((unsigned)sr >> 16);
         }
         return h;
     };
+    // FP32 screen with the FP64 decision inside the error band
+    auto pair_in = [&](int j) -> bool {
+        float4 o = pos4[j];
+        float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float hsum = p.w + o.w;
+        float hs2 = hsum * hsum;
+        float d = r2 - hs2;
+        float M = fmaf(c1, hsum, 3.2e-6f * hs2);
+        bool in = d < -M;
+        if (fabsf(d) <= M) {
+            ++nre;
+            in = pair_in_fp64(xs[i], ys[i], zs[i], hs[i], xs[j], ys[j], zs[j], hs[j]);
+        }
+        return in;
+    };
 
-    unsigned stack[kStackCap];
     int sp = 0;
     int ncand = 0;
     const int top = tl.nlevels - 1;
     if (top == 0) {
         int64_t gi = tl.offset[0];
-        unsigned m = __ballot_sync(0xffffffffu, box_hit(nodes[2 * gi], nodes[2 * gi + 1]));
+        unsigned m = __ballot_sync(0xffffffffu, sub == 0 && box_hit(nodes[2 * gi], nodes[2 * gi + 1]));
         if (m) {
             if (lane == 0) {
                 s_leaf[warp][0] = 0;
-                s_mask[warp][0] = m;
+                s_mask[warp][0] = (unsigned char)(m & 0xffu);
             }
             ncand = 1;
         }
     } else {
-        stack[sp++] = ((unsigned)top << 26) | 0u;
+        if (lane == 0) stack[0] = ((unsigned)top << 26) | 0u;
+        sp = 1;
     }
+    __syncwarp();
     while (true) {
         while (sp > 0 && ncand <= kCandCap - kBranch) {
-            unsigned e = stack[--sp];
+            unsigned e = stack[sp - 1];
+            --sp;
+            __syncwarp();
             int lv = (int)(e >> 26), k = (int)(e & ((1u << 26) - 1u));
             int c0 = kBranch * k;
             int nc = min(kBranch, tl.count[lv - 1] - c0);
             int64_t base = (int64_t)tl.offset[lv - 1] + c0;
-            unsigned hm[kBranch];
+            unsigned bal[2];
 #pragma unroll
-            for (int c = 0; c < kBranch; ++c) {
-                int cc = c < nc ? c : 0;
-                float4 a = nodes[2 * (base + cc)], b = nodes[2 * (base + cc) + 1];
-                hm[c] = __ballot_sync(0xffffffffu, c < nc && box_hit(a, b));
+            for (int r = 0; r < 2; ++r) {
+                int c = 4 * r + sub;
+                bool hit = false;
+                if (c < nc) hit = box_hit(nodes[2 * (base + c)], nodes[2 * (base + c) + 1]);
+                bal[r] = __ballot_sync(0xffffffffu, hit);
             }
+            // lane c < 8: particle mask of child c
+            const int c = lane & 7;
+            unsigned cm = ((c < 4 ? bal[0] : bal[1]) >> (8 * (c & 3))) & 0xffu;
+            bool mine = lane < kBranch && cm != 0u;
+            unsigned any = __ballot_sync(0xffffffffu, mine);
+            int nh = __popc(any), rank = __popc(any & lt_mask);
             if (lv == 1) {
-#pragma unroll
-                for (int c = 0; c < kBranch; ++c) {
-                    if (hm[c]) {
-                        if (lane == 0) {
-                            s_leaf[warp][ncand] = c0 + c;
-                            s_mask[warp][ncand] = hm[c];
-                        }
-                        ++ncand;
-                    }
+                if (mine) {
+                    s_leaf[warp][ncand + rank] = c0 + c;
+                    s_mask[warp][ncand + rank] = (unsigned char)cm;
                 }
+                ncand += nh;
             } else {
-#pragma unroll
-                for (int c = kBranch - 1; c >= 0; --c)
-                    if (hm[c]) stack[sp++] = ((unsigned)(lv - 1) << 26) | (unsigned)(c0 + c);
+                if (mine) stack[sp + nh - 1 - rank] = ((unsigned)(lv - 1) << 26) | (unsigned)(c0 + c);
+                sp += nh;
             }
+            __syncwarp();
         }
-        __syncwarp();
         int cpos = 0;
         while (true) {
-            while (cpos < ncand && !((s_mask[warp][cpos] >> lane) & 1u)) ++cpos;
+            while (cpos < ncand && !((s_mask[warp][cpos] >> q) & 1u)) ++cpos;
             bool have = cpos < ncand;
             if (!__any_sync(0xffffffffu, have)) break;
+            bool in0 = false, in1 = false;
+            int js = 0;
             if (have) {
                 int leaf = s_leaf[warp][cpos];
                 ++cpos;
-                int j0 = leaf_start[leaf], j1 = leaf_start[leaf + 1];
-                float4 q[kLeaf];
-#pragma unroll
-                for (int t = 0; t < kLeaf; ++t) q[t] = pos4[j0 + t < j1 ? j0 + t : j0];
-#pragma unroll
-                for (int t = 0; t < kLeaf; ++t) {
-                    int j = j0 + t;
-                    float dx = p.x - q[t].x, dy = p.y - q[t].y, dz = p.z - q[t].z;
-                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float hsum = p.w + q[t].w;
-                    float hs2 = hsum * hsum;
-                    float d = r2 - hs2;
-                    float M = fmaf(c1, hsum, 3.2e-6f * hs2);
-                    bool in = d < -M;
-                    if (fabsf(d) <= M && j < j1 && j != (int)i) {
-                        ++nre;
-                        in = pair_in_fp64(xs[i], ys[i], zs[i], hs[i], xs[j], ys[j], zs[j], hs[j]);
-                    }
-                    if (in && j < j1 && j != (int)i) {
-                        if (cnt < cap) out[cnt] = j;
-                        else over = true;
-                        ++cnt;
-                    }
-                }
+                js = leaf_start[leaf];
+                int je = leaf_start[leaf + 1];
+                int ja = js + sub, jb = js + sub + 4;
+                in0 = ja < je && ja != (int)i && pair_in(ja);
+                in1 = jb < je && jb != (int)i && pair_in(jb);
             }
+            unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
+            // hit mask of this lane's particle: bit t for the leaf's particle t
+            unsigned m8 = 0;
+#pragma unroll
+            for (int s = 0; s < kSub; ++s)
+                m8 |= (((b0 >> (kGroup * s + q)) & 1u) << s) | (((b1 >> (kGroup * s + q)) & 1u) << (s + 4));
+            if (in0) {
+                int pos = cnt + __popc(m8 & ((1u << sub) - 1u));
+                if (pos < cap) out[pos] = js + sub;
+                else over = true;
+            }
+            if (in1) {
+                int pos = cnt + __popc(m8 & ((1u << (sub + 4)) - 1u));
+                if (pos < cap) out[pos] = js + sub + 4;
+                else over = true;
+            }
+            cnt += __popc(m8);
         }
         __syncwarp();
         ncand = 0;
         if (sp == 0) break;
     }
-    if (valid) ncnt[i] = cnt < cap ? cnt : cap;
-    pairs += (unsigned long long)(cnt < cap ? cnt : cap);
+    if (valid && sub == 0) ncnt[i] = cnt < cap ? cnt : cap;
+    if (sub == 0) pairs += (unsigned long long)(cnt < cap ? cnt : cap);
     }  // group loop
     // counters: one atomic per warp
     unsigned long long c = pairs;
@@ -642,7 +675,7 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_neighbors<false>, kListThreads, 0);
         if (sms < 1) sms = 1;
     }
-    const int64_t need = (n + kListThreads - 1) / kListThreads;
+    const int64_t need = (n + kGroup * kListWarps - 1) / (kGroup * kListWarps);
     int64_t cap_blocks = (int64_t)sms * ((multi_star ? per_sm_t : per_sm_f) > 0 ? (multi_star ? per_sm_t : per_sm_f) : 1);
     const int lb = (int)(need < cap_blocks ? need : cap_blocks);
     if (multi_star)

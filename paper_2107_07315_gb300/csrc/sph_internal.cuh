@@ -16,9 +16,11 @@
 //                  (rho, P, dP/drho, h_enth), (W~, c_s, D, 0).
 //   nbr[n*cap]   : neighbour list of each sorted particle (sorted indices,
 //                  ascending), ncnt[n] its length.
-//   tree nodes   : implicit binary tree over leaves of 8 consecutive sorted
+//   pos4[n]      : float4 fl32(x, y, z, h) per sorted particle, read by the
+//                  FP32 screening of the list build.
+//   tree nodes   : implicit 8-ary tree over leaves of 8 consecutive sorted
 //                  particles of one star; node = float4 (lo.xyz, h_max) +
-//                  float4 (hi.xyz, star range packed in an int).
+//                  float4 (hi.xyz, star range packed in the float bits).
 #pragma once
 
 #include <cstdint>
