@@ -422,6 +422,10 @@ constexpr int kListThreads = 64;
 constexpr int kListWarps = kListThreads / 32;
 constexpr int kGroup = 8;                              // particles per warp
 constexpr int kSub = 32 / kGroup;                      // lanes per particle
+constexpr int kChildRounds = kBranch / kSub;           // child tests per lane and node
+constexpr int kLeafRounds = kLeaf / kSub;              // pair tests per lane and leaf
+static_assert(kGroup * kSub == 32 && kGroup <= 16 && kChildRounds >= 1 && kLeafRounds >= 1,
+              "group shape");
 constexpr int kCandCap = 160;                          // candidate leaves buffered per warp
 constexpr int kStackCap = (kBranch - 1) * 10 + 2;      // depth bound for <= 10 levels
 
@@ -455,7 +459,7 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             int32_t *ncnt, DevScalars *sc)
 {
     __shared__ int s_leaf[kListWarps][kCandCap];
-    __shared__ unsigned char s_mask[kListWarps][kCandCap];
+    __shared__ unsigned short s_mask[kListWarps][kCandCap];
     __shared__ unsigned s_stack[kListWarps][kStackCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = lane & (kGroup - 1), sub = lane / kGroup;
@@ -524,7 +528,7 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
         if (m) {
             if (lane == 0) {
                 s_leaf[warp][0] = 0;
-                s_mask[warp][0] = (unsigned char)(m & 0xffu);
+                s_mask[warp][0] = (unsigned short)(m & ((1u << kGroup) - 1u));
             }
             ncand = 1;
         }
@@ -542,24 +546,28 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             int c0 = kBranch * k;
             int nc = min(kBranch, tl.count[lv - 1] - c0);
             int64_t base = (int64_t)tl.offset[lv - 1] + c0;
-            unsigned bal[2];
+            unsigned bal[kChildRounds];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                int c = 4 * r + sub;
+            for (int r = 0; r < kChildRounds; ++r) {
+                int c = kSub * r + sub;
                 bool hit = false;
                 if (c < nc) hit = box_hit(nodes[2 * (base + c)], nodes[2 * (base + c) + 1]);
                 bal[r] = __ballot_sync(0xffffffffu, hit);
             }
             // lane c < 8: particle mask of child c
-            const int c = lane & 7;
-            unsigned cm = ((c < 4 ? bal[0] : bal[1]) >> (8 * (c & 3))) & 0xffu;
+            const int c = lane & (kBranch - 1);
+            unsigned bc = bal[0];
+#pragma unroll
+            for (int r = 1; r < kChildRounds; ++r)
+                if (c / kSub == r) bc = bal[r];
+            unsigned cm = (bc >> (kGroup * (c % kSub))) & ((1u << kGroup) - 1u);
             bool mine = lane < kBranch && cm != 0u;
             unsigned any = __ballot_sync(0xffffffffu, mine);
             int nh = __popc(any), rank = __popc(any & lt_mask);
             if (lv == 1) {
                 if (mine) {
                     s_leaf[warp][ncand + rank] = c0 + c;
-                    s_mask[warp][ncand + rank] = (unsigned char)cm;
+                    s_mask[warp][ncand + rank] = (unsigned short)cm;
                 }
                 ncand += nh;
             } else {
@@ -573,32 +581,39 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             while (cpos < ncand && !((s_mask[warp][cpos] >> q) & 1u)) ++cpos;
             bool have = cpos < ncand;
             if (!__any_sync(0xffffffffu, have)) break;
-            bool in0 = false, in1 = false;
+            bool in[kLeafRounds];
             int js = 0;
             if (have) {
                 int leaf = s_leaf[warp][cpos];
                 ++cpos;
                 js = leaf_start[leaf];
                 int je = leaf_start[leaf + 1];
-                int ja = js + sub, jb = js + sub + 4;
-                in0 = ja < je && ja != (int)i && pair_in(ja);
-                in1 = jb < je && jb != (int)i && pair_in(jb);
+#pragma unroll
+                for (int u = 0; u < kLeafRounds; ++u) {
+                    int j = js + kSub * u + sub;
+                    in[u] = j < je && j != (int)i && pair_in(j);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < kLeafRounds; ++u) in[u] = false;
             }
-            unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
             // hit mask of this lane's particle: bit t for the leaf's particle t
             unsigned m8 = 0;
 #pragma unroll
-            for (int s = 0; s < kSub; ++s)
-                m8 |= (((b0 >> (kGroup * s + q)) & 1u) << s) | (((b1 >> (kGroup * s + q)) & 1u) << (s + 4));
-            if (in0) {
-                int pos = cnt + __popc(m8 & ((1u << sub) - 1u));
-                if (pos < cap) out[pos] = js + sub;
-                else over = true;
+            for (int u = 0; u < kLeafRounds; ++u) {
+                unsigned b = __ballot_sync(0xffffffffu, in[u]);
+#pragma unroll
+                for (int s = 0; s < kSub; ++s)
+                    m8 |= ((b >> (kGroup * s + q)) & 1u) << (kSub * u + s);
             }
-            if (in1) {
-                int pos = cnt + __popc(m8 & ((1u << (sub + 4)) - 1u));
-                if (pos < cap) out[pos] = js + sub + 4;
-                else over = true;
+#pragma unroll
+            for (int u = 0; u < kLeafRounds; ++u) {
+                if (in[u]) {
+                    int t = kSub * u + sub;
+                    int pos = cnt + __popc(m8 & ((1u << t) - 1u));
+                    if (pos < cap) out[pos] = js + t;
+                    else over = true;
+                }
             }
             cnt += __popc(m8);
         }
