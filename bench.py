@@ -480,25 +480,42 @@ def oracle_sample_rhs(st, eos, met, sample: int, seed: int):
     return pairs, t1 - t0, ids, r
 
 
-def auto_sample(st, eos, met, target_s: float) -> int:
-    """Particle sample whose oracle right-hand side takes about target_s."""
-    oracle_sample_rhs(st, eos, met, min(200, len(st["x"])), 2)  # thread start-up
-    cal = min(4000, len(st["x"]))
-    _, sec, _, _ = oracle_sample_rhs(st, eos, met, cal, 3)
-    return int(min(len(st["x"]), max(cal, cal * target_s / max(sec, 1e-3))))
+def oracle_full_rhs(st, eos, met):
+    """Oracle right-hand side of every particle; returns (pairs, seconds, rates)."""
+    import oracle
+    from paper_2107_07315_gb300 import inputs as I
+
+    t0 = time.perf_counter()
+    r = oracle.rhs(st, eos, I.DEFAULT_MATERIAL, met, scales=True)
+    t1 = time.perf_counter()
+    return float(r["ncount"].sum()), t1 - t0, r
 
 
-def cpu_baseline(st, eos, met, sample: int):
+def cpu_baseline(st, eos, met, sample: int, min_seconds: float = 10.0):
+    """The oracle timed on the host cores.
+
+    sample <= 0: the full right-hand side of the star, repeated until at least
+    min_seconds have passed (at most 4 times).  Its cost is nearly that of any
+    sample, because the density of every neighbour of the sampled particles
+    is needed.  sample > 0: one sampled right-hand side of that many particles.
+    """
     import oracle
 
-    if sample <= 0:
-        sample = auto_sample(st, eos, met, 15.0)
-    pairs, sec, ids, r = oracle_sample_rhs(st, eos, met, sample, 7)
+    if sample > 0:
+        pairs, sec, ids, r = oracle_sample_rhs(st, eos, met, sample, 7)
+        what = ("right-hand side of %d random particles of the %d-particle star "
+                "(brute-force O(N^2) neighbour search over all particles, FP64), %.1f s"
+                % (sample, len(st["x"]), sec))
+    else:
+        pairs, sec, reps = 0.0, 0.0, 0
+        while reps < 4 and (reps == 0 or sec < min_seconds):
+            p, t, r = oracle_full_rhs(st, eos, met)
+            pairs, sec, reps = pairs + p, sec + t, reps + 1
+        ids = np.arange(len(st["x"]), dtype=np.int64)
+        what = ("full right-hand side of the %d-particle star, %d time(s) (brute-force O(N^2) "
+                "neighbour search, FP64), %.1f s in total" % (len(st["x"]), reps, sec))
     return {"value": pairs / sec, "unit": "pairs/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "right-hand side of %d random particles of the %d-particle star "
-                      "(brute-force O(N^2) neighbour search over all particles, FP64), "
-                      "%.1f s" % (sample, len(st["x"]), sec)}, ids, r
+            "kind": "oracle", "sample": what}, ids, r
 
 
 def parity_errors(g, o, ids):
@@ -579,15 +596,15 @@ def run_reference(args):
 
     st, eos, met, _ = make_star(1, args.n)
     sample = args.cpu_sample
-    if sample <= 0:
-        # per step a bounded sample: the whole run stays within a few minutes
-        per_step = min(20.0, 150.0 / max(args.steps, 1))
-        sample = auto_sample(st, eos, met, per_step)
     for k in range(args.warmup):
-        oracle_sample_rhs(st, eos, met, max(sample // 16, 16), 100 + k)
+        oracle_sample_rhs(st, eos, met, min(500, len(st["x"])), 100 + k)
     tot_p, tot_s = 0.0, 0.0
     for k in range(args.steps):
-        p, s, _, _ = oracle_sample_rhs(st, eos, met, sample, 200 + k)
+        # one step: the full right-hand side (or a sample of --cpu-sample particles)
+        if sample > 0:
+            p, s, _, _ = oracle_sample_rhs(st, eos, met, sample, 200 + k)
+        else:
+            p, s, _ = oracle_full_rhs(st, eos, met)
         tot_p += p
         tot_s += s
     v = tot_p / tot_s
@@ -595,13 +612,14 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": "TOV star, %d particles, FP64 CPU oracle right-hand side on "
-                                  "a bounded particle sample per step" % len(st["x"]),
+           "config": {"workload": "TOV star, %d particles, FP64 CPU oracle right-hand side "
+                                  "per step" % len(st["x"]),
                       "n_particles": len(st["x"])},
            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": oracle.num_threads(),
                             "kind": "oracle",
-                            "sample": "%d random particles per step, brute-force neighbours"
-                                      % sample},
+                            "sample": ("%d random particles per step" % sample if sample > 0
+                                       else "full right-hand side per step")
+                                      + ", brute-force O(N^2) neighbours, FP64"},
            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -620,7 +638,7 @@ def main():
     ap.add_argument("--nstars", type=int, default=64)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--cpu-sample", type=int, default=0,
-                    help="oracle particle sample; 0 sizes it to about 15 s of host time")
+                    help="oracle particle sample; 0 times the full right-hand side")
     ap.add_argument("--fp64-steps", type=int, default=5,
                     help="timed steps of the plain FP64 path on the same star (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

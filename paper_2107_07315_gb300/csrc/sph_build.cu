@@ -426,7 +426,15 @@ constexpr int kChildRounds = kBranch / kSub;           // child tests per lane a
 constexpr int kLeafRounds = kLeaf / kSub;              // pair tests per lane and leaf
 static_assert(kGroup * kSub == 32 && kGroup <= 16 && kChildRounds >= 1 && kLeafRounds >= 1,
               "group shape");
-constexpr int kCandCap = 160;                          // candidate leaves buffered per warp
+// bit kGroup*s set for s = 0 .. kSub-1: picks one particle's bits out of a ballot
+constexpr unsigned spread_bits()
+{
+    unsigned m = 0;
+    for (int s = 0; s < kSub; ++s) m |= 1u << (kGroup * s);
+    return m;
+}
+constexpr unsigned kSpread = spread_bits();
+constexpr int kCandCap = 256;                          // candidate leaves buffered per warp
 constexpr int kStackCap = (kBranch - 1) * 10 + 2;      // depth bound for <= 10 levels
 
 // One warp per 8 consecutive sorted particles, four lanes per particle:
@@ -458,7 +466,7 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             const int32_t *leaf_of, TreeLevels tl, const float4 *nodes, int cap, int32_t *nbr,
             int32_t *ncnt, DevScalars *sc)
 {
-    __shared__ int s_leaf[kListWarps][kCandCap];
+    __shared__ int2 s_leaf[kListWarps][kCandCap];    // particle range of a buffered leaf
     __shared__ unsigned short s_mask[kListWarps][kCandCap];
     __shared__ unsigned s_stack[kListWarps][kStackCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -527,7 +535,7 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
         unsigned m = __ballot_sync(0xffffffffu, sub == 0 && box_hit(nodes[2 * gi], nodes[2 * gi + 1]));
         if (m) {
             if (lane == 0) {
-                s_leaf[warp][0] = 0;
+                s_leaf[warp][0] = make_int2(leaf_start[0], leaf_start[1]);
                 s_mask[warp][0] = (unsigned short)(m & ((1u << kGroup) - 1u));
             }
             ncand = 1;
@@ -566,7 +574,7 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             int nh = __popc(any), rank = __popc(any & lt_mask);
             if (lv == 1) {
                 if (mine) {
-                    s_leaf[warp][ncand + rank] = c0 + c;
+                    s_leaf[warp][ncand + rank] = make_int2(leaf_start[c0 + c], leaf_start[c0 + c + 1]);
                     s_mask[warp][ncand + rank] = (unsigned short)cm;
                 }
                 ncand += nh;
@@ -584,10 +592,10 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             bool in[kLeafRounds];
             int js = 0;
             if (have) {
-                int leaf = s_leaf[warp][cpos];
+                const int2 lr = s_leaf[warp][cpos];
                 ++cpos;
-                js = leaf_start[leaf];
-                int je = leaf_start[leaf + 1];
+                js = lr.x;
+                const int je = lr.y;
 #pragma unroll
                 for (int u = 0; u < kLeafRounds; ++u) {
                     int j = js + kSub * u + sub;
@@ -597,25 +605,20 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
 #pragma unroll
                 for (int u = 0; u < kLeafRounds; ++u) in[u] = false;
             }
-            // hit mask of this lane's particle: bit t for the leaf's particle t
-            unsigned m8 = 0;
+            // a hit of leaf particle t = kSub u + sub goes after the particle's
+            // hits of earlier rounds and of lower sub-lanes in this round
+            int pre = cnt;
 #pragma unroll
             for (int u = 0; u < kLeafRounds; ++u) {
-                unsigned b = __ballot_sync(0xffffffffu, in[u]);
-#pragma unroll
-                for (int s = 0; s < kSub; ++s)
-                    m8 |= ((b >> (kGroup * s + q)) & 1u) << (kSub * u + s);
-            }
-#pragma unroll
-            for (int u = 0; u < kLeafRounds; ++u) {
+                const unsigned b = (__ballot_sync(0xffffffffu, in[u]) >> q) & kSpread;
                 if (in[u]) {
-                    int t = kSub * u + sub;
-                    int pos = cnt + __popc(m8 & ((1u << t) - 1u));
-                    if (pos < cap) out[pos] = js + t;
+                    int pos = pre + __popc(b & ((1u << (kGroup * sub)) - 1u));
+                    if (pos < cap) out[pos] = js + kSub * u + sub;
                     else over = true;
                 }
+                pre += __popc(b);
             }
-            cnt += __popc(m8);
+            cnt = pre;
         }
         __syncwarp();
         ncand = 0;
