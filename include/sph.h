@@ -133,7 +133,7 @@ sph_status sph_init(sph_ctx **out, const sph_particles *particles, const sph_eos
                     const sph_material *material, const sph_metric *metric,
                     sph_precision precision, const sph_options *options, void *cuda_stream);
 
-/* Right-hand side at the bound state: Morton sort, neighbour lists, density
+/* Right-hand side at the bound state: Hilbert-curve sort, neighbour lists, density
  * summation (Sec. I.C "standard formula"), equation of state, pair sums of
  * Eqs. solid1-solid6, stress rate (Eq. solid4) and background force
  * (Sec. I.C), written to *out (device arrays of the caller).  Asynchronous. */
@@ -168,7 +168,7 @@ sph_status sph_totals(sph_ctx *ctx, double out[16]);
  * evaluated, 3 kernel launches in one step, 4 tree leaves, 5 marginal pairs
  * re-checked in FP64 (cumulative), 6 neighbour capacity per particle,
  * 7 lanes per particle, 8 1 if steps run as a CUDA graph, 9 steps taken,
- * 10 radix passes, 11 Morton bits per axis.  Synchronous. */
+ * 10 radix passes, 11 cell bits per axis of the curve key.  Synchronous. */
 sph_status sph_stats(sph_ctx *ctx, int64_t out[16]);
 
 /* Device-time measurement with CUDA events on the context's stream.

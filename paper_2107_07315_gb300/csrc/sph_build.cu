@@ -1,4 +1,4 @@
-// Neighbour search: bounding box, Morton keys, LSD radix sort, sorted
+// Neighbour search: bounding box, Hilbert keys, LSD radix sort, sorted
 // gather, leaf tree and exact per-particle neighbour lists.
 //
 // The neighbour predicate is the one of Sec. I.B: b is a neighbour of a iff
@@ -143,7 +143,44 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v)
     return v;
 }
 
-// Morton key (star id above 3*bits interleaved cell bits) and identity value.
+// Hilbert index of cell (x0, x1, x2), `bits` bits per axis.  Skilling's
+// transform (J. Skilling, "Programming the Hilbert curve", AIP Conf. Proc. 707,
+// 2004) turns the coordinates into the transposed index in place: per level,
+// from the top, a set bit inverts the lower bits of the first axis, a clear
+// bit exchanges them with those of its own axis; a Gray decode follows.  The
+// transposed index read bit-plane by bit-plane is the position on the curve.
+// Consecutive cells on the curve share a face, so runs of consecutive sorted
+// particles (the tree leaves) are more compact than along a Morton curve.
+__device__ __forceinline__ uint32_t hilbert3(uint32_t x0, uint32_t x1, uint32_t x2, int bits)
+{
+    uint32_t X[3] = {x0, x1, x2};
+    const uint32_t top = 1u << (bits - 1);
+    for (uint32_t Q = top; Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = top; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    X[0] ^= t;
+    X[1] ^= t;
+    X[2] ^= t;
+    return spread3(X[2]) | (spread3(X[1]) << 1) | (spread3(X[0]) << 2);
+}
+
+// Space-filling-curve key (star id above the 3*bits bits of the cell's Hilbert
+// index) and identity value.
 __global__ void k_keys(DevState st, const DevScalars *sc, int bits,
                        unsigned long long *keys, uint32_t *vals)
 {
@@ -159,8 +196,7 @@ __global__ void k_keys(DevState st, const DevScalars *sc, int bits,
         t = fmin(fmax(t, 0.0), cells - 1.0);
         q[k] = (uint32_t)t;
     }
-    unsigned long long key = (unsigned long long)(spread3(q[0]) | (spread3(q[1]) << 1) |
-                                                  (spread3(q[2]) << 2));
+    unsigned long long key = (unsigned long long)hilbert3(q[0], q[1], q[2], bits);
     uint32_t s = st.star ? (uint32_t)st.star[i] : 0u;
     key |= (unsigned long long)s << (3 * bits);
     keys[i] = key;

@@ -1,6 +1,6 @@
 // Internal declarations shared by the libsph translation units.
 //
-// Data layout in device memory (n particles, "sorted" = Morton order):
+// Data layout in device memory (n particles, "sorted" = Hilbert-curve order):
 //   caller order : the caller's state and rate buffers (borrowed).
 //   perm[n]      : sorted slot -> caller index (int32).
 //   xs,ys,zs,hs  : FP64 sorted positions and smoothing lengths.
@@ -50,7 +50,7 @@ struct DevScalars {
     unsigned long long bbox_hi[3];
     double grid;                     // Xhi grid spacing (power of two)
     double grid_inv;                 // 1/grid (exact)
-    double inv_ext[3];               // 1/(bbox extent) per axis, for Morton keys
+    double inv_ext[3];               // 1/(bbox extent) per axis, for the curve keys
     double eps_abs;                  // absolute slack for tree pruning
     float screen_c1;                 // FP32 screening band coefficient (1.67e-6 max|x|)
     int err;                         // ERR_* bits
@@ -151,7 +151,7 @@ struct Scratch {
 
 // Launch helpers implemented in sph_build.cu.
 struct SortPlan {
-    int key_bits_axis;  // Morton bits per axis
+    int key_bits_axis;  // cell bits per axis of the curve key
     int star_bits;
     int passes;         // 8-bit digit passes
     int ipt;            // items per thread in sort kernels
