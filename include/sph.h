@@ -201,7 +201,7 @@ void sph_free(sph_ctx *ctx);
  * sph_neighbors for one star: x, y, z, h are device arrays of n particles
  * (caller order), offsets a device int64[n+1], idx a device int32[cap];
  * cuda_stream a cudaStream_t (NULL: legacy default stream).  Scratch is one
- * fixed device array of about 10.6 MB inside the library, present on every
+ * fixed device array of about 11.7 MB inside the library, present on every
  * GPU that loads it until the process exits; limits: n <= 16384 (larger n
  * returns SPH_ERR_ARG) and at most 128 neighbours per particle
  * (SPH_ERR_CAPACITY).  The first call on a device looks up the array's

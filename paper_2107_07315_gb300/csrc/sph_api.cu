@@ -455,7 +455,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     STATUS_TRY(c->alloc(&s.keys[1], nn));
     STATUS_TRY(c->alloc(&s.vals[0], nn));
     STATUS_TRY(c->alloc(&s.vals[1], nn));
-    STATUS_TRY(c->alloc(&s.hist, (size_t)c->plan.passes * 256 * c->plan.nblocks));
+    STATUS_TRY(c->alloc(&s.hist, (size_t)c->plan.passes * 256 * c->plan.nblocks * 2));
     STATUS_TRY(c->alloc(&s.radix_tot, (size_t)8 * 256));
     STATUS_TRY(c->alloc(&s.xs, nn));
     STATUS_TRY(c->alloc(&s.ys, nn));

@@ -34,7 +34,8 @@ constexpr int kBoxThreads = 256;
 // Bounding box of all positions.  Each block writes a partial; the last
 // block to finish reduces the partials, derives the position grid and
 // resets the per-RHS counters.  Also flags non-finite positions and h.
-__global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScalars *sc)
+__global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScalars *sc,
+                       uint32_t *radix_tot)
 {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     bool bad = false;
@@ -80,6 +81,9 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
     }
     __syncthreads();
     if (!last) return;
+    // the sort of this right-hand side starts from zero digit totals and tile counters
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) radix_tot[k] = 0u;
+    if (threadIdx.x < 8) sc->tile_next[threadIdx.x] = 0u;
     // all threads of the last block reduce the block partials
     for (int k = 0; k < 3; ++k) {
         double a = 1e300, b = -1e300;
@@ -179,143 +183,180 @@ __device__ __forceinline__ uint32_t hilbert3(uint32_t x0, uint32_t x1, uint32_t 
     return spread3(X[2]) | (spread3(X[1]) << 1) | (spread3(X[0]) << 2);
 }
 
-// Space-filling-curve key (star id above the 3*bits bits of the cell's Hilbert
-// index) and identity value.
-__global__ void k_keys(DevState st, const DevScalars *sc, int bits,
-                       unsigned long long *keys, uint32_t *vals)
+constexpr int kSortThreads = 256;
+constexpr int kMaxPasses = 8;
+constexpr int kSpinLimit = 1 << 22;  // look-back polls before giving up (error flag)
+
+// Space-filling-curve key of every particle (star id above the 3*bits bits of
+// the cell's Hilbert index), its identity value, and the digit histograms of
+// all radix passes at once (a digit count does not depend on the key order).
+// Also clears the tile status words of all passes.
+__global__ void k_keys_hist(DevState st, const DevScalars *sc, int bits, int passes,
+                            unsigned long long *keys, uint32_t *vals, uint32_t *radix_tot,
+                            unsigned long long *status, int64_t status_words)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= st.n) return;
-    double p[3] = {st.x[i], st.y[i], st.z[i]};
-    uint32_t q[3];
-    double cells = (double)(1u << bits);
+    __shared__ uint32_t h[kMaxPasses][256];
+    for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0u;
+    __syncthreads();
+    const double cells = (double)(1u << bits);
+    double lo[3], inv[3];
     for (int k = 0; k < 3; ++k) {
-        double lo = dec_double(sc->bbox_lo[k]), hi = dec_double(sc->bbox_hi[k]);
-        double ext = hi - lo;
-        double t = ext > 0.0 ? (p[k] - lo) * sc->inv_ext[k] * cells : 0.0;
-        t = fmin(fmax(t, 0.0), cells - 1.0);
-        q[k] = (uint32_t)t;
+        lo[k] = dec_double(sc->bbox_lo[k]);
+        inv[k] = sc->inv_ext[k];
     }
-    unsigned long long key = (unsigned long long)hilbert3(q[0], q[1], q[2], bits);
-    uint32_t s = st.star ? (uint32_t)st.star[i] : 0u;
-    key |= (unsigned long long)s << (3 * bits);
-    keys[i] = key;
-    vals[i] = (uint32_t)i;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double p[3] = {st.x[i], st.y[i], st.z[i]};
+        uint32_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            double t = inv[k] > 0.0 ? (p[k] - lo[k]) * inv[k] * cells : 0.0;
+            t = fmin(fmax(t, 0.0), cells - 1.0);
+            q[k] = (uint32_t)t;
+        }
+        unsigned long long key = (unsigned long long)hilbert3(q[0], q[1], q[2], bits);
+        uint32_t s = st.star ? (uint32_t)st.star[i] : 0u;
+        key |= (unsigned long long)s << (3 * bits);
+        keys[i] = key;
+        vals[i] = (uint32_t)i;
+        for (int pp = 0; pp < passes; ++pp) atomicAdd(&h[pp][(key >> (8 * pp)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        uint32_t c = h[p][threadIdx.x];
+        if (c) atomicAdd(&radix_tot[p * 256 + threadIdx.x], c);
+    }
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < status_words;
+         w += (int64_t)gridDim.x * blockDim.x)
+        status[w] = 0ull;
 }
 
-constexpr int kSortThreads = 256;
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
-// Per-tile digit histogram of one pass over the keys in their current order
-// (the tiles of pass p hold different keys than those of pass p-1, so each
-// pass counts its own).  hist layout: [digit][block].
-__global__ void k_radix_hist(const unsigned long long *keys, int64_t n, int ipt, int shift,
-                             uint32_t *hist, uint32_t *digit_total)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// One stable 8-bit digit pass in a single launch.  Blocks claim tiles in
+// order from a counter, so every lower tile belongs to a block that is
+// already running.  A tile counts its digits, publishes the counts (status
+// word: 1 = tile count, 2 = inclusive prefix over tiles, value in the low 32
+// bits), and thread d then walks back over lower tiles adding their counts
+// until it meets a published prefix (decoupled look-back).  Keys are then
+// scattered to base(d) + prefix + rank, the rank stable within the tile.
+// A poll that never sees a lower tile's word gives up after kSpinLimit
+// tries and raises ERR_TIMEOUT (the sort is then invalid, the host reports it).
+__global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
+                           unsigned long long *kout, uint32_t *vout, int64_t n, int ipt,
+                           int shift, const uint32_t *digit_total, unsigned long long *status,
+                           unsigned int *tile_next, DevScalars *sc)
 {
     __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0u;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortThreads * ipt;
-    for (int r = 0; r < ipt; ++r) {
-        int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    uint32_t c = cnt[threadIdx.x];
-    hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = c;
-    if (c) atomicAdd(&digit_total[threadIdx.x], c);
-}
-
-// Exclusive offsets of one pass: block d handles digit d.  Its base is the
-// number of keys with a smaller digit (sum of the digit totals below d); the
-// row of per-tile counts is then scanned in tile order.
-__global__ void k_radix_scan(uint32_t *hist, const uint32_t *digit_total, int nblocks)
-{
-    __shared__ uint32_t wsum[8];
-    const int d = blockIdx.x, t = threadIdx.x;
-    const int lane = t & 31, w = t >> 5;
-    // base = sum of totals of digits < d
-    uint32_t v = t < d ? digit_total[t] : 0u;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wsum[w] = v;
-    __syncthreads();
-    uint32_t base = 0;
-    for (int k = 0; k < 8; ++k) base += wsum[k];
-    __syncthreads();
-    // scan of the row hist[d][0 .. nblocks)
-    uint32_t *h = hist + (int64_t)d * nblocks;
-    int chunk = (nblocks + 255) / 256;
-    int b0 = t * chunk, b1 = min(b0 + chunk, nblocks);
-    uint32_t s = 0;
-    for (int i = b0; i < b1; ++i) s += h[i];
-    uint32_t x = s;
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wsum[kSortThreads / 32];
+    __shared__ uint32_t wc[kSortThreads / 32][256];
+    __shared__ int s_tile;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) s_tile = (int)atomicAdd(tile_next, 1u);
+    cnt[t] = 0u;
+    // base of digit t: keys of this pass with a smaller digit
+    const uint32_t tot = digit_total[t];
+    uint32_t x = tot;
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) wsum[w] = x;
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    uint32_t woff = 0;
-    for (int k = 0; k < w; ++k) woff += wsum[k];
-    uint32_t run = base + woff + x - s;
-    for (int i = b0; i < b1; ++i) {
-        uint32_t c = h[i];
-        h[i] = run;
-        run += c;
-    }
-}
-
-// Stable scatter of one 8-bit digit pass.
-__global__ void k_radix_scatter(const unsigned long long *kin, const uint32_t *vin,
-                                unsigned long long *kout, uint32_t *vout, int64_t n, int ipt,
-                                int shift, const uint32_t *hist_scanned)
-{
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wc[kSortThreads / 32][256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run[threadIdx.x] = hist_scanned[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
-    const unsigned lt = (1u << lane) - 1u;
-    int64_t base = (int64_t)blockIdx.x * kSortThreads * ipt;
+    uint32_t base = x - tot;
+    for (int w = 0; w < warp; ++w) base += wsum[w];
+    const int tile = s_tile;
+    const int64_t first = (int64_t)tile * kSortThreads * ipt;
     for (int r = 0; r < ipt; ++r) {
-        int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+        int64_t i = first + (int64_t)r * kSortThreads + t;
+        if (i < n) atomicAdd(&cnt[(kin[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    const uint32_t c = cnt[t];
+    unsigned long long *mine = status + (int64_t)tile * 256 + t;
+    uint32_t excl = 0u;
+    if (tile == 0) {
+        st_release_u64(mine, (2ull << 32) | c);
+    } else {
+        st_release_u64(mine, (1ull << 32) | c);
+        int k = tile - 1;
+        int polls = 0;
+        while (k >= 0) {
+            unsigned long long w = ld_acquire_u64(status + (int64_t)k * 256 + t);
+            uint32_t f = (uint32_t)(w >> 32);
+            if (f == 0u) {
+                if (++polls > kSpinLimit) {
+                    atomicOr(&sc->err, ERR_TIMEOUT);
+                    break;
+                }
+                continue;
+            }
+            excl += (uint32_t)w;
+            if (f == 2u) break;
+            --k;
+        }
+        st_release_u64(mine, (2ull << 32) | (excl + c));
+    }
+    run[t] = base + excl;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < ipt; ++r) {
+        int64_t i = first + (int64_t)r * kSortThreads + t;
         bool valid = i < n;
         unsigned long long k = valid ? kin[i] : 0ull;
         uint32_t v = valid ? vin[i] : 0u;
         uint32_t d = valid ? (uint32_t)((k >> shift) & 255u) : 256u;
-        for (int w = 0; w < kSortThreads / 32; ++w) wc[w][threadIdx.x] = 0u;
+        for (int w = 0; w < kSortThreads / 32; ++w) wc[w][t] = 0u;
         __syncthreads();
         unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t rank = __popc(peers & lt);
         if (valid && (__ffs(peers) - 1) == lane) wc[warp][d] = __popc(peers);
         __syncthreads();
-        uint32_t tot = 0;
-        {
-            int t = threadIdx.x;
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                uint32_t c = wc[w][t];
-                wc[w][t] = tot;
-                tot += c;
-            }
+        uint32_t acc = 0;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            uint32_t cw = wc[w][t];
+            wc[w][t] = acc;
+            acc += cw;
         }
         __syncthreads();
         if (valid) {
             uint32_t dst = run[d] + wc[warp][d] + rank;
-            kout[dst] = k;
-            vout[dst] = v;
+            if ((int64_t)dst < n) {
+                kout[dst] = k;
+                vout[dst] = v;
+            } else {  // only after a failed look-back (ERR_TIMEOUT is set too)
+                atomicOr(&sc->err, ERR_BOUNDS);
+            }
         }
         __syncthreads();
-        run[threadIdx.x] += tot;
+        run[t] += acc;
         __syncthreads();
     }
 }
 
 // Sorted copies and the FP32 j-record halves read by the list build.
-__global__ void k_gather(DevState st, const uint32_t *order, const DevScalars *sc, int32_t *perm,
+__global__ void k_gather(DevState st, const uint32_t *order, DevScalars *sc, int32_t *perm,
                          double *xs, double *ys, double *zs, double *hs, uint8_t *tys,
                          float4 *rec, float4 *pos4, double4_32a *rec64)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= st.n) return;
-    int32_t c = (int32_t)order[i];
+    uint32_t o = order[i];
+    if ((int64_t)o >= st.n) {  // only after a failed sort (its error flag is set too)
+        atomicOr(&sc->err, ERR_BOUNDS);
+        o = 0u;
+    }
+    int32_t c = (int32_t)o;
     perm[i] = c;
     double p[3] = {st.x[c], st.y[c], st.z[c]};
     double h = st.h[c], m = st.m[c];
@@ -354,11 +395,12 @@ __device__ __forceinline__ float4 node_merge_b(float4 a, float4 b)
                        __int_as_float((int)((unsigned)lo | ((unsigned)hi << 16))));
 }
 
-// Leaf boxes and the implicit 8-ary tree above them.  Boxes are rounded
-// outward to FP32 so that they contain every FP64 position of the node.
-__global__ void k_tree(const double *xs, const double *ys, const double *zs, const double *hs,
-                       const int32_t *leaf_start, const int32_t *leaf_star, TreeLevels tl,
-                       float4 *nodes, DevScalars *sc)
+// Leaf boxes and the implicit 8-ary tree above them.  Leaf boxes come from
+// pos4 = fl32(x, y, z, h) widened by one FP32 ulp outward: a round-to-nearest
+// value lies within half an ulp of the FP64 value, so the widened box holds
+// every FP64 position (and h_max bounds every FP64 h) of the leaf.
+__global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int32_t *leaf_star,
+                       TreeLevels tl, float4 *nodes, DevScalars *sc)
 {
     __shared__ float4 sa[kTreeBlock], sb[kTreeBlock];
     const int t = threadIdx.x;
@@ -366,20 +408,27 @@ __global__ void k_tree(const double *xs, const double *ys, const double *zs, con
     const int nleaves = tl.count[0];
     float4 a = make_float4(3e38f, 3e38f, 3e38f, 0.f), b = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
     if (l < nleaves) {
-        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, hm = 0.0;
-        for (int i = leaf_start[l]; i < leaf_start[l + 1]; ++i) {
-            double p[3] = {xs[i], ys[i], zs[i]};
-            for (int k = 0; k < 3; ++k) {
-                lo[k] = fmin(lo[k], p[k]);
-                hi[k] = fmax(hi[k], p[k]);
-            }
-            hm = fmax(hm, hs[i]);
+        const int j0 = leaf_start[l], j1 = leaf_start[l + 1];
+        float4 q[kLeaf];
+#pragma unroll
+        for (int k = 0; k < kLeaf; ++k) q[k] = pos4[j0 + k < j1 ? j0 + k : j0];
+        float lo[3] = {q[0].x, q[0].y, q[0].z}, hi[3] = {q[0].x, q[0].y, q[0].z}, hm = q[0].w;
+#pragma unroll
+        for (int k = 1; k < kLeaf; ++k) {
+            lo[0] = fminf(lo[0], q[k].x);
+            lo[1] = fminf(lo[1], q[k].y);
+            lo[2] = fminf(lo[2], q[k].z);
+            hi[0] = fmaxf(hi[0], q[k].x);
+            hi[1] = fmaxf(hi[1], q[k].y);
+            hi[2] = fmaxf(hi[2], q[k].z);
+            hm = fmaxf(hm, q[k].w);
         }
+        const float ninf = -INFINITY, pinf = INFINITY;
         int s = leaf_star[l];
-        a = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]),
-                        __double2float_rd(lo[2]), __double2float_ru(hm));
-        b = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]),
-                        __double2float_ru(hi[2]), __int_as_float((int)((unsigned)s | ((unsigned)s << 16))));
+        a = make_float4(nextafterf(lo[0], ninf), nextafterf(lo[1], ninf), nextafterf(lo[2], ninf),
+                        nextafterf(hm, pinf));
+        b = make_float4(nextafterf(hi[0], pinf), nextafterf(hi[1], pinf), nextafterf(hi[2], pinf),
+                        __int_as_float((int)((unsigned)s | ((unsigned)s << 16))));
         nodes[2 * ((int64_t)tl.offset[0] + l) + 0] = a;
         nodes[2 * ((int64_t)tl.offset[0] + l) + 1] = b;
     }
@@ -690,30 +739,34 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     int64_t nb = (n + kBoxThreads - 1) / kBoxThreads;
     int bblocks = (int)(nb < kBoxBlocksMax ? nb : kBoxBlocksMax);
     if (bblocks < 1) bblocks = 1;
-    k_bbox<<<bblocks, kBoxThreads, 0, stream>>>(st, s.bbox_partial, s.bbox_done, s.sc);
+    k_bbox<<<bblocks, kBoxThreads, 0, stream>>>(st, s.bbox_partial, s.bbox_done, s.sc,
+                                                 s.radix_tot);
     ++nl;
-    int tb = 256;
-    int gb = (int)((n + tb - 1) / tb);
-    k_keys<<<gb, tb, 0, stream>>>(st, s.sc, plan.key_bits_axis, s.keys[0], s.vals[0]);
+    // keys, all digit histograms and cleared tile status words in one launch
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(s.hist);
+    const int64_t status_words = (int64_t)plan.passes * plan.nblocks * 256;
+    int kb = (int)((n + kSortThreads - 1) / kSortThreads);
+    if (kb > 2 * kBoxBlocksMax) kb = 2 * kBoxBlocksMax;
+    k_keys_hist<<<kb, kSortThreads, 0, stream>>>(st, s.sc, plan.key_bits_axis, plan.passes,
+                                                 s.keys[0], s.vals[0], s.radix_tot, status,
+                                                 status_words);
     ++nl;
-    cudaMemsetAsync(s.radix_tot, 0, sizeof(uint32_t) * 256 * plan.passes, stream);
     for (int p = 0; p < plan.passes; ++p) {
         int src = p & 1, dst = src ^ 1;
-        uint32_t *hist = s.hist + (int64_t)p * 256 * plan.nblocks;
-        uint32_t *tot = s.radix_tot + 256 * p;
-        k_radix_hist<<<plan.nblocks, kSortThreads, 0, stream>>>(s.keys[src], n, plan.ipt, 8 * p,
-                                                                hist, tot);
-        k_radix_scan<<<256, 256, 0, stream>>>(hist, tot, plan.nblocks);
-        k_radix_scatter<<<plan.nblocks, kSortThreads, 0, stream>>>(
-            s.keys[src], s.vals[src], s.keys[dst], s.vals[dst], n, plan.ipt, 8 * p, hist);
-        nl += 3;
+        k_onesweep<<<plan.nblocks, kSortThreads, 0, stream>>>(
+            s.keys[src], s.vals[src], s.keys[dst], s.vals[dst], n, plan.ipt, 8 * p,
+            s.radix_tot + 256 * p, status + (int64_t)p * plan.nblocks * 256, &s.sc->tile_next[p],
+            s.sc);
+        ++nl;
     }
     const uint32_t *order = s.vals[plan.passes & 1];
+    const int tb = 256;
+    const int gb = (int)((n + tb - 1) / tb);
     k_gather<<<gb, tb, 0, stream>>>(st, order, s.sc, s.perm, s.xs, s.ys, s.zs, s.hs, s.tys, s.rec,
                                     s.pos4, fp64_records ? s.rec64 : nullptr);
     ++nl;
     k_tree<<<(nleaves + kTreeBlock - 1) / kTreeBlock, kTreeBlock, 0, stream>>>(
-        s.xs, s.ys, s.zs, s.hs, s.leaf_start, s.leaf_star, tl, s.nodes, s.sc);
+        s.pos4, s.leaf_start, s.leaf_star, tl, s.nodes, s.sc);
     ++nl;
     if (ev_lists) {
         if (ev_external) cudaEventRecordWithFlags(ev_lists, stream, cudaEventRecordExternal);

@@ -56,6 +56,7 @@ struct DevScalars {
     int err;                         // ERR_* bits
     int tree_done;                   // block counter of the tree kernel
     unsigned int list_next;          // next particle group of the neighbour kernel
+    unsigned int tile_next[8];       // next sort tile of each radix pass
     unsigned long long pairs_last;   // ordered pairs of the last RHS
     unsigned long long pairs_total;
     unsigned long long rechecks;     // marginal FP64 predicate evaluations
@@ -127,7 +128,7 @@ struct Scratch {
     int32_t *perm;
     unsigned long long *keys[2];
     uint32_t *vals[2];
-    uint32_t *hist;           // [passes][256][nblocks]
+    uint32_t *hist;           // sort tile status: [passes][nblocks][256] 64-bit words
     uint32_t *radix_tot;      // [8][256] digit totals per pass
     double *xs, *ys, *zs, *hs;
     uint8_t *tys;             // sorted type

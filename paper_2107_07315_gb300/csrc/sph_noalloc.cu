@@ -11,7 +11,7 @@
 // first call before any stream capture.
 //
 // Limits: at most kMaxN particles of one star, at most kCap neighbours per
-// particle.  The array (about 10.6 MB) exists on every GPU that loads this
+// particle.  The array (about 11.7 MB) exists on every GPU that loads this
 // library and stays there until the process exits.  All calls share it:
 // calls that overlap on the GPU (different streams or threads without
 // ordering between them) race on it.
@@ -39,7 +39,7 @@ constexpr size_t kKeys1 = kKeys0 + align256(kMaxN * 8);
 constexpr size_t kVals0 = kKeys1 + align256(kMaxN * 8);
 constexpr size_t kVals1 = kVals0 + align256(kMaxN * 4);
 constexpr size_t kHist = kVals1 + align256(kMaxN * 4);
-constexpr size_t kXs = kHist + align256((size_t)kMaxPasses * 256 * kMaxSortBlocks * 4);
+constexpr size_t kXs = kHist + align256((size_t)kMaxPasses * 256 * kMaxSortBlocks * 8);
 constexpr size_t kYs = kXs + align256(kMaxN * 8);
 constexpr size_t kZs = kYs + align256(kMaxN * 8);
 constexpr size_t kHs = kZs + align256(kMaxN * 8);
@@ -200,6 +200,7 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
         cudaStreamSynchronize(stream) != cudaSuccess)
         return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: kernel or copy failed");
     if (err & ERR_NONFINITE) return fail(SPH_ERR_NONFINITE, "sph_neighbors_noalloc: non-finite x or h");
+    if (err & ERR_TIMEOUT) return fail(SPH_ERR_TIMEOUT, "sph_neighbors_noalloc: sort wait timed out");
     if (err & ERR_CAPACITY)
         return fail(SPH_ERR_CAPACITY, "sph_neighbors_noalloc: a particle has more than 128 neighbours");
     if (tot > cap) return fail(SPH_ERR_CAPACITY, "sph_neighbors_noalloc: lists exceed cap");
