@@ -17,12 +17,6 @@ namespace sph {
 
 namespace {
 
-__device__ __forceinline__ unsigned long long enc_double(double d)
-{
-    unsigned long long u = (unsigned long long)__double_as_longlong(d);
-    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
-}
-
 __device__ __forceinline__ double dec_double(unsigned long long e)
 {
     unsigned long long u = (e & 0x8000000000000000ull) ? (e & ~0x8000000000000000ull) : ~e;
@@ -31,31 +25,51 @@ __device__ __forceinline__ double dec_double(unsigned long long e)
 
 constexpr int kBoxThreads = 256;
 
+// Order-preserving integer image of a double's bits (dec_double inverts it).
+__device__ __forceinline__ unsigned long long enc_bits(unsigned long long u)
+{
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ bool finite_bits(unsigned long long u)
+{
+    return ((u >> 52) & 0x7ffull) != 0x7ffull;
+}
+
 // Bounding box of all positions.  Each block writes a partial; the last
 // block to finish reduces the partials, derives the position grid and
 // resets the per-RHS counters.  Also flags non-finite positions and h.
-__global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScalars *sc,
-                       uint32_t *radix_tot)
+// Minima and maxima are taken on order-preserving integer images of the
+// doubles, which keeps the scan off the (narrow) FP64 pipe.
+__global__ void k_bbox(DevState st, unsigned long long *partial, unsigned int *done,
+                       DevScalars *sc, uint32_t *radix_tot)
 {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double p[3] = {st.x[i], st.y[i], st.z[i]};
-        double hh = st.h[i];
-        bad |= !(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(hh) && hh > 0.0);
+        unsigned long long p[3] = {(unsigned long long)__double_as_longlong(st.x[i]),
+                                   (unsigned long long)__double_as_longlong(st.y[i]),
+                                   (unsigned long long)__double_as_longlong(st.z[i])};
+        long long hb = __double_as_longlong(st.h[i]);
+        // h must be finite and > 0: sign clear, not zero, exponent not all ones
+        bad |= !(finite_bits(p[0]) && finite_bits(p[1]) && finite_bits(p[2]) &&
+                 finite_bits((unsigned long long)hb) && hb > 0);
         for (int k = 0; k < 3; ++k) {
-            lo[k] = fmin(lo[k], p[k]);
-            hi[k] = fmax(hi[k], p[k]);
+            unsigned long long e = enc_bits(p[k]);
+            lo[k] = e < lo[k] ? e : lo[k];
+            hi[k] = e > hi[k] ? e : hi[k];
         }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&sc->err, ERR_NONFINITE);
-    __shared__ double s_lo[3][kBoxThreads / 32], s_hi[3][kBoxThreads / 32];
+    __shared__ unsigned long long s_lo[3][kBoxThreads / 32], s_hi[3][kBoxThreads / 32];
     for (int k = 0; k < 3; ++k) {
-        double a = lo[k], b = hi[k];
+        unsigned long long a = lo[k], b = hi[k];
         for (int o = 16; o > 0; o >>= 1) {
-            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+            unsigned long long ao = __shfl_xor_sync(0xffffffffu, a, o);
+            unsigned long long bo = __shfl_xor_sync(0xffffffffu, b, o);
+            a = ao < a ? ao : a;
+            b = bo > b ? bo : b;
         }
         if ((threadIdx.x & 31) == 0) {
             s_lo[k][threadIdx.x >> 5] = a;
@@ -65,10 +79,10 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
     __syncthreads();
     if (threadIdx.x < 3) {
         int k = threadIdx.x;
-        double a = s_lo[k][0], b = s_hi[k][0];
+        unsigned long long a = s_lo[k][0], b = s_hi[k][0];
         for (int w = 1; w < kBoxThreads / 32; ++w) {
-            a = fmin(a, s_lo[k][w]);
-            b = fmax(b, s_hi[k][w]);
+            a = s_lo[k][w] < a ? s_lo[k][w] : a;
+            b = s_hi[k][w] > b ? s_hi[k][w] : b;
         }
         partial[blockIdx.x * 6 + k] = a;
         partial[blockIdx.x * 6 + 3 + k] = b;
@@ -86,14 +100,17 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
     if (threadIdx.x < 8) sc->tile_next[threadIdx.x] = 0u;
     // all threads of the last block reduce the block partials
     for (int k = 0; k < 3; ++k) {
-        double a = 1e300, b = -1e300;
+        unsigned long long a = ~0ull, b = 0ull;
         for (int w = threadIdx.x; w < (int)gridDim.x; w += blockDim.x) {
-            a = fmin(a, __ldcg(&partial[w * 6 + k]));
-            b = fmax(b, __ldcg(&partial[w * 6 + 3 + k]));
+            unsigned long long pa = __ldcg(&partial[w * 6 + k]), pb = __ldcg(&partial[w * 6 + 3 + k]);
+            a = pa < a ? pa : a;
+            b = pb > b ? pb : b;
         }
         for (int o = 16; o > 0; o >>= 1) {
-            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+            unsigned long long ao = __shfl_xor_sync(0xffffffffu, a, o);
+            unsigned long long bo = __shfl_xor_sync(0xffffffffu, b, o);
+            a = ao < a ? ao : a;
+            b = bo > b ? bo : b;
         }
         if ((threadIdx.x & 31) == 0) {
             s_lo[k][threadIdx.x >> 5] = a;
@@ -103,13 +120,13 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
     __syncthreads();
     if (threadIdx.x < 3) {
         int k = threadIdx.x;
-        double a = s_lo[k][0], b = s_hi[k][0];
+        unsigned long long a = s_lo[k][0], b = s_hi[k][0];
         for (int w = 1; w < kBoxThreads / 32; ++w) {
-            a = fmin(a, s_lo[k][w]);
-            b = fmax(b, s_hi[k][w]);
+            a = s_lo[k][w] < a ? s_lo[k][w] : a;
+            b = s_hi[k][w] > b ? s_hi[k][w] : b;
         }
-        sc->bbox_lo[k] = enc_double(a);
-        sc->bbox_hi[k] = enc_double(b);
+        sc->bbox_lo[k] = a;
+        sc->bbox_hi[k] = b;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -123,9 +140,14 @@ __global__ void k_bbox(DevState st, double *partial, unsigned int *done, DevScal
         frexp(fmax(m, 1e-300), &e);  // m < 2^e
         sc->grid = ldexp(1.0, e - 22);
         sc->grid_inv = ldexp(1.0, 22 - e);
+        sc->grid_f = (float)sc->grid;
+        sc->grid_inv_f = (float)sc->grid_inv;
         for (int k = 0; k < 3; ++k) {
-            double ext = dec_double(sc->bbox_hi[k]) - dec_double(sc->bbox_lo[k]);
+            double lo_k = dec_double(sc->bbox_lo[k]);
+            double ext = dec_double(sc->bbox_hi[k]) - lo_k;
             sc->inv_ext[k] = ext > 0.0 ? 1.0 / ext : 0.0;
+            sc->key_lo_f[k] = (float)lo_k;
+            sc->key_scale_f[k] = (float)sc->inv_ext[k];
         }
         sc->eps_abs = 1e-6 * fmax(m, 1e-30);
         sc->screen_c1 = (float)(1.67e-6 * m);
@@ -198,19 +220,22 @@ __global__ void k_keys_hist(DevState st, const DevScalars *sc, int bits, int pas
     __shared__ uint32_t h[kMaxPasses][256];
     for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0u;
     __syncthreads();
-    const double cells = (double)(1u << bits);
-    double lo[3], inv[3];
+    // cell coordinates in FP32 (any fixed map of position to cell serves the
+    // ordering; the clamp absorbs rounding at the box faces)
+    const float cells = (float)(1u << bits);
+    float lo[3], sc3[3];
     for (int k = 0; k < 3; ++k) {
-        lo[k] = dec_double(sc->bbox_lo[k]);
-        inv[k] = sc->inv_ext[k];
+        lo[k] = sc->key_lo_f[k];
+        sc3[k] = sc->key_scale_f[k] * cells;
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double p[3] = {st.x[i], st.y[i], st.z[i]};
+        const float p[3] = {__double2float_rn(st.x[i]), __double2float_rn(st.y[i]),
+                            __double2float_rn(st.z[i])};
         uint32_t q[3];
         for (int k = 0; k < 3; ++k) {
-            double t = inv[k] > 0.0 ? (p[k] - lo[k]) * inv[k] * cells : 0.0;
-            t = fmin(fmax(t, 0.0), cells - 1.0);
+            float t = (p[k] - lo[k]) * sc3[k];
+            t = fminf(fmaxf(t, 0.f), cells - 1.f);
             q[k] = (uint32_t)t;
         }
         unsigned long long key = (unsigned long long)hilbert3(q[0], q[1], q[2], bits);
@@ -230,17 +255,21 @@ __global__ void k_keys_hist(DevState st, const DevScalars *sc, int bits, int pas
         status[w] = 0ull;
 }
 
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+// Tile status words hold a flag and a count in one aligned 64-bit word, so
+// relaxed single-copy-atomic accesses suffice: no other data hangs on them.
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+
+constexpr int kLookback = 8;  // predecessor words read together per look-back step
 
 // One stable 8-bit digit pass in a single launch.  Blocks claim tiles in
 // order from a counter, so every lower tile belongs to a block that is
@@ -249,6 +278,9 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // bits), and thread d then walks back over lower tiles adding their counts
 // until it meets a published prefix (decoupled look-back).  Keys are then
 // scattered to base(d) + prefix + rank, the rank stable within the tile.
+// Look-back reads kLookback lower tiles per step, so a tile whose
+// predecessors have only published counts still finds its prefix in a few
+// steps instead of waiting for a chain of prefixes.
 // A poll that never sees a lower tile's word gives up after kSpinLimit
 // tries and raises ERR_TIMEOUT (the sort is then invalid, the host reports it).
 __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
@@ -286,26 +318,40 @@ __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
     unsigned long long *mine = status + (int64_t)tile * 256 + t;
     uint32_t excl = 0u;
     if (tile == 0) {
-        st_release_u64(mine, (2ull << 32) | c);
+        st_relaxed_u64(mine, (2ull << 32) | c);
     } else {
-        st_release_u64(mine, (1ull << 32) | c);
+        st_relaxed_u64(mine, (1ull << 32) | c);
         int k = tile - 1;
         int polls = 0;
         while (k >= 0) {
-            unsigned long long w = ld_acquire_u64(status + (int64_t)k * 256 + t);
-            uint32_t f = (uint32_t)(w >> 32);
-            if (f == 0u) {
-                if (++polls > kSpinLimit) {
-                    atomicOr(&sc->err, ERR_TIMEOUT);
-                    break;
+            // read up to kLookback lower tiles at once, then add them in order
+            // until a prefix (done) or a word not yet written (poll again)
+            unsigned long long w[kLookback];
+#pragma unroll
+            for (int u = 0; u < kLookback; ++u)
+                w[u] = u <= k ? ld_relaxed_u64(status + (int64_t)(k - u) * 256 + t) : (2ull << 32);
+            bool done = false, stall = false;
+            int used = 0;
+#pragma unroll
+            for (int u = 0; u < kLookback; ++u) {
+                if (done || stall) continue;
+                uint32_t f = (uint32_t)(w[u] >> 32);
+                if (f == 0u) {
+                    stall = true;
+                } else {
+                    if (u <= k) excl += (uint32_t)w[u];
+                    used = u + 1;
+                    done = f == 2u;
                 }
-                continue;
             }
-            excl += (uint32_t)w;
-            if (f == 2u) break;
-            --k;
+            k -= used;
+            if (done) break;
+            if (stall && ++polls > kSpinLimit) {
+                atomicOr(&sc->err, ERR_TIMEOUT);
+                break;
+            }
         }
-        st_release_u64(mine, (2ull << 32) | (excl + c));
+        st_relaxed_u64(mine, (2ull << 32) | (excl + c));
     }
     run[t] = base + excl;
     __syncthreads();
@@ -344,6 +390,23 @@ __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
     }
 }
 
+// A float as a double, by moving its exponent and mantissa bits (exact for
+// zero and normal floats; subnormals take the conversion instruction).
+__device__ __forceinline__ double float_to_double_exact(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t ex = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if (ex == 0u) {
+        if (man == 0u) return __longlong_as_double((long long)sign);
+        return (double)f;
+    }
+    if (ex == 0xffu) return (double)f;
+    const unsigned long long bits =
+        sign | ((unsigned long long)(ex - 127u + 1023u) << 52) | ((unsigned long long)man << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 // Sorted copies and the FP32 j-record halves read by the list build.
 __global__ void k_gather(DevState st, const uint32_t *order, DevScalars *sc, int32_t *perm,
                          double *xs, double *ys, double *zs, double *hs, uint8_t *tys,
@@ -365,16 +428,20 @@ __global__ void k_gather(DevState st, const uint32_t *order, DevScalars *sc, int
     zs[i] = p[2];
     hs[i] = h;
     tys[i] = st.type[c];
-    double g = sc->grid;
-    float hi[3], lo[3];
+    // Two-float split: Xhi = g * rint(fl32(x)/g) on the power-of-two grid g
+    // (exact in FP32 since |x|/g < 2^22), Xlo = fl32(x - Xhi) with the
+    // difference taken exactly in FP64; |x - Xhi| <= 3g/4.
+    const float gf = sc->grid_f, gi = sc->grid_inv_f;
+    float xf[3], hi[3], lo[3];
     for (int k = 0; k < 3; ++k) {
-        double H = g * rint(p[k] * sc->grid_inv);  // grid is a power of two: exact
-        hi[k] = (float)H;
-        lo[k] = (float)(p[k] - H);
+        xf[k] = __double2float_rn(p[k]);
+        hi[k] = rintf(xf[k] * gi) * gf;
+        lo[k] = __double2float_rn(p[k] - float_to_double_exact(hi[k]));
     }
-    rec[i * 4 + 0] = make_float4(hi[0], hi[1], hi[2], (float)h);
-    rec[i * 4 + 1] = make_float4(lo[0], lo[1], lo[2], (float)m);
-    pos4[i] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)h);
+    const float hf = __double2float_rn(h);
+    rec[i * 4 + 0] = make_float4(hi[0], hi[1], hi[2], hf);
+    rec[i * 4 + 1] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(m));
+    pos4[i] = make_float4(xf[0], xf[1], xf[2], hf);
     if (rec64) {
         rec64[i * 3 + 0] = make_double4_32a(p[0], p[1], p[2], h);
         rec64[i * 3 + 1].x = m;
@@ -739,8 +806,8 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     int64_t nb = (n + kBoxThreads - 1) / kBoxThreads;
     int bblocks = (int)(nb < kBoxBlocksMax ? nb : kBoxBlocksMax);
     if (bblocks < 1) bblocks = 1;
-    k_bbox<<<bblocks, kBoxThreads, 0, stream>>>(st, s.bbox_partial, s.bbox_done, s.sc,
-                                                 s.radix_tot);
+    k_bbox<<<bblocks, kBoxThreads, 0, stream>>>(
+        st, reinterpret_cast<unsigned long long *>(s.bbox_partial), s.bbox_done, s.sc, s.radix_tot);
     ++nl;
     // keys, all digit histograms and cleared tile status words in one launch
     unsigned long long *status = reinterpret_cast<unsigned long long *>(s.hist);

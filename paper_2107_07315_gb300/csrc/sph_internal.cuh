@@ -51,6 +51,8 @@ struct DevScalars {
     double grid;                     // Xhi grid spacing (power of two)
     double grid_inv;                 // 1/grid (exact)
     double inv_ext[3];               // 1/(bbox extent) per axis, for the curve keys
+    float key_lo_f[3], key_scale_f[3];  // FP32 copies of the box corner and 1/extent
+    float grid_f, grid_inv_f;        // FP32 copies of grid and 1/grid (powers of two)
     double eps_abs;                  // absolute slack for tree pruning
     float screen_c1;                 // FP32 screening band coefficient (1.67e-6 max|x|)
     int err;                         // ERR_* bits
