@@ -503,7 +503,7 @@ __global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int3
     sb[t] = b;
     __syncthreads();
     // In-block levels: node k of level v+1 is the union of nodes 8k..8k+7 of
-    // level v.  A block of 512 leaves holds three such levels.
+    // level v.  A block of kTreeBlock = 8^kTreeBlockLevels leaves holds that many levels.
     int top_local = min(tl.nlevels - 1, kTreeBlockLevels);
     for (int v = 1; v <= top_local; ++v) {
         int width = kTreeBlock >> (3 * v);

@@ -33,8 +33,8 @@ namespace sph {
 constexpr int kLeaf = 8;          // particles per tree leaf
 constexpr int kBranch = 8;        // children per tree node
 constexpr int kMaxLevels = 16;
-constexpr int kTreeBlock = 512;   // leaves per block in the tree kernel (8^3)
-constexpr int kTreeBlockLevels = 3;
+constexpr int kTreeBlock = 64;    // leaves per block in the tree kernel (8^2)
+constexpr int kTreeBlockLevels = 2;
 
 // Device error word bits.
 enum : int {
