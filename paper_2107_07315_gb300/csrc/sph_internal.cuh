@@ -6,7 +6,7 @@
 //   xs,ys,zs,hs  : FP64 sorted positions and smoothing lengths.
 //   rec[n][4]    : float4 j-record per sorted particle:
 //                  0 (Xhi.x, Xhi.y, Xhi.z, h)  1 (Xlo.x, Xlo.y, Xlo.z, m)
-//                  2 (v.x, v.y, v.z, D)         3 (P/D^2, c_s, 1/D, 0)
+//                  2 (v.x, v.y, v.z, D)         3 (P/D^2, c_s, 1/D, solid)
 //                  Xhi + Xlo is the FP64 position split into an FP32 value
 //                  on a power-of-two grid and an FP32 remainder.
 //   rec64[n][3]  : double4_32a j-record of the FP64 path: (x,y,z,h), (m,vx,vy,vz),

@@ -193,7 +193,7 @@ k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevR
     const float invD = 1.f / D;
     const float PD2 = p.P * invD * invD;
     s.rec[i * 4 + 2] = make_float4(vx, vy, vz, D);
-    s.rec[i * 4 + 3] = make_float4(PD2, p.cs, invD, 0.f);
+    s.rec[i * 4 + 3] = make_float4(PD2, p.cs, invD, s.tys[i] == 1 ? 1.f : 0.f);
     if (s.tys[i] == 1) {
         const int64_t N = st.n;
         const float f = invD * invD;
@@ -410,7 +410,7 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
             const int j = list[k];
             const float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
             const float4 q2 = s.rec[(int64_t)j * 4 + 2], q3 = s.rec[(int64_t)j * 4 + 3];
-            const bool solid_j = s.tys[j] == 1;
+            const bool solid_j = q3.w != 0.f;  // type rides in the record: no extra load
             float dx = (a0.x - q0.x) + (a1.x - q1.x);
             float dy = (a0.y - q0.y) + (a1.y - q1.y);
             float dz = (a0.z - q0.z) + (a1.z - q1.z);
