@@ -599,8 +599,17 @@ def run_reference(args):
 
     st, eos, met, _ = make_star(1, args.n)
     sample = args.cpu_sample
-    for k in range(args.warmup):
-        oracle_sample_rhs(st, eos, met, min(500, len(st["x"])), 100 + k)
+    n = len(st["x"])
+    if sample <= 0:
+        # one full right-hand side per step when the run fits in ~150 s; else a
+        # particle sample (its cost is mostly the density of the sample's
+        # neighbours, about 61 per particle, each summed over all particles)
+        _, t_full, _ = oracle_full_rhs(st, eos, met)
+        budget = 150.0 / max(args.steps, 1)
+        if t_full > budget:
+            sample = max(64, min(n, int(n / 61.0 * budget / t_full)))
+    for k in range(max(args.warmup - 1, 0)):
+        oracle_sample_rhs(st, eos, met, min(500, n), 100 + k)
     tot_p, tot_s = 0.0, 0.0
     for k in range(args.steps):
         # one step: the full right-hand side (or a sample of --cpu-sample particles)
