@@ -439,8 +439,8 @@ __global__ void k_gather(DevState st, const uint32_t *order, DevScalars *sc, int
         lo[k] = __double2float_rn(p[k] - float_to_double_exact(hi[k]));
     }
     const float hf = __double2float_rn(h);
-    rec[i * 4 + 0] = make_float4(hi[0], hi[1], hi[2], hf);
-    rec[i * 4 + 1] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(m));
+    rec[i] = make_float4(hi[0], hi[1], hi[2], hf);
+    rec[st.n + i] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(m));
     pos4[i] = make_float4(xf[0], xf[1], xf[2], hf);
     if (rec64) {
         rec64[i * 3 + 0] = make_double4_32a(p[0], p[1], p[2], h);

@@ -4,14 +4,17 @@
 //   caller order : the caller's state and rate buffers (borrowed).
 //   perm[n]      : sorted slot -> caller index (int32).
 //   xs,ys,zs,hs  : FP64 sorted positions and smoothing lengths.
-//   rec[n][4]    : float4 j-record per sorted particle:
+//   rec[4][n]    : float4 j-record of each sorted particle, one array per
+//                  field (structure of arrays: a warp gathering one field of
+//                  nearby neighbours touches few cache lines):
 //                  0 (Xhi.x, Xhi.y, Xhi.z, h)  1 (Xlo.x, Xlo.y, Xlo.z, m)
 //                  2 (v.x, v.y, v.z, D)         3 (P/D^2, c_s, 1/D, solid)
 //                  Xhi + Xlo is the FP64 position split into an FP32 value
 //                  on a power-of-two grid and an FP32 remainder.
 //   rec64[n][3]  : double4_32a j-record of the FP64 path: (x,y,z,h), (m,vx,vy,vz),
 //                  (D, 1/D, P/D^2, c_s).
-//   sd2 / sd264  : S/D^2 per sorted particle, 2 float4 or 8 doubles.
+//   sd2 / sd264  : S/D^2 per sorted particle: sd2[2][n] float4 (xx,yy,zz,xy),
+//                  (xz,yz,0,0); sd264[n][8] doubles.
 //   pp / pp64    : per-particle EoS values for the finalize step:
 //                  (rho, P, dP/drho, h_enth), (W~, c_s, D, 0).
 //   nbr[n*cap]   : neighbour list of each sorted particle (sorted indices,
@@ -134,10 +137,10 @@ struct Scratch {
     uint32_t *radix_tot;      // [8][256] digit totals per pass
     double *xs, *ys, *zs, *hs;
     uint8_t *tys;             // sorted type
-    float4 *rec;              // [n][4]
+    float4 *rec;              // [4][n]
     float4 *pos4;             // [n] fl32(x, y, z, h) for neighbour screening
     double4_32a *rec64;           // [n][3]
-    float4 *sd2;              // [n][2]
+    float4 *sd2;              // [2][n]
     double *sd264;            // [n][8]
     float4 *pp;               // [n][2]
     double *pp64;             // [n][8]

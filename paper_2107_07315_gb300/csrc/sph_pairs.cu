@@ -149,14 +149,14 @@ k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevR
         const int cnt = valid ? s.ncnt[i] : 0;
         float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid) {
-            a0 = s.rec[i * 4 + 0];
-            a1 = s.rec[i * 4 + 1];
+            a0 = s.rec[i];
+            a1 = s.rec[n + i];
         }
         float sum = 0.f, comp = 0.f;
         const int32_t *list = s.nbr + i * (int64_t)cap;
         for (int k = sub; k < cnt; k += LPI) {
             int j = list[k];
-            float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
+            float4 q0 = s.rec[j], q1 = s.rec[n + j];
             float dx = (a0.x - q0.x) + (a1.x - q1.x);
             float dy = (a0.y - q0.y) + (a1.y - q1.y);
             float dz = (a0.z - q0.z) + (a1.z - q1.z);
@@ -192,18 +192,18 @@ k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevR
     Prep<float> p = eos_prep<float>(eos, g, star, D, vx, vy, vz, s.xs[i], s.ys[i], s.zs[i]);
     const float invD = 1.f / D;
     const float PD2 = p.P * invD * invD;
-    s.rec[i * 4 + 2] = make_float4(vx, vy, vz, D);
-    s.rec[i * 4 + 3] = make_float4(PD2, p.cs, invD, s.tys[i] == 1 ? 1.f : 0.f);
+    s.rec[2 * n + i] = make_float4(vx, vy, vz, D);
+    s.rec[3 * n + i] = make_float4(PD2, p.cs, invD, s.tys[i] == 1 ? 1.f : 0.f);
     if (s.tys[i] == 1) {
         const int64_t N = st.n;
         const float f = invD * invD;
-        s.sd2[i * 2 + 0] = make_float4((float)st.S[c] * f, (float)st.S[N + c] * f,
+        s.sd2[i] = make_float4((float)st.S[c] * f, (float)st.S[N + c] * f,
                                        (float)st.S[2 * N + c] * f, (float)st.S[3 * N + c] * f);
-        s.sd2[i * 2 + 1] = make_float4((float)st.S[4 * N + c] * f, (float)st.S[5 * N + c] * f,
+        s.sd2[n + i] = make_float4((float)st.S[4 * N + c] * f, (float)st.S[5 * N + c] * f,
                                        0.f, 0.f);
     } else {
-        s.sd2[i * 2 + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s.sd2[i * 2 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s.sd2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s.sd2[n + i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     s.pp[i * 2 + 0] = make_float4(p.rho, p.P, p.cP, p.henth);
     s.pp[i * 2 + 1] = make_float4(p.Wt, p.cs, D, 0.f);
@@ -391,14 +391,14 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
                as1 = as0;
         bool solid_i = false;
         if (valid) {
-            a0 = s.rec[i * 4 + 0];
-            a1 = s.rec[i * 4 + 1];
-            a2 = s.rec[i * 4 + 2];
-            a3 = s.rec[i * 4 + 3];
+            a0 = s.rec[i];
+            a1 = s.rec[n + i];
+            a2 = s.rec[2 * n + i];
+            a3 = s.rec[3 * n + i];
             solid_i = s.tys[i] == 1;
             if (solid_i) {
-                as0 = s.sd2[i * 2 + 0];
-                as1 = s.sd2[i * 2 + 1];
+                as0 = s.sd2[i];
+                as1 = s.sd2[n + i];
             }
         }
         float aP0 = 0.f, aP1 = 0.f, aP2 = 0.f, aX0 = 0.f, aX1 = 0.f, aX2 = 0.f;
@@ -408,8 +408,8 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
         const int32_t *list = s.nbr + i * (int64_t)cap;
         for (int k = sub; k < cnt; k += LPI) {
             const int j = list[k];
-            const float4 q0 = s.rec[(int64_t)j * 4 + 0], q1 = s.rec[(int64_t)j * 4 + 1];
-            const float4 q2 = s.rec[(int64_t)j * 4 + 2], q3 = s.rec[(int64_t)j * 4 + 3];
+            const float4 q0 = s.rec[j], q1 = s.rec[n + j];
+            const float4 q2 = s.rec[2 * n + j], q3 = s.rec[3 * n + j];
             const bool solid_j = q3.w != 0.f;  // type rides in the record: no extra load
             float dx = (a0.x - q0.x) + (a1.x - q1.x);
             float dy = (a0.y - q0.y) + (a1.y - q1.y);
@@ -453,8 +453,8 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
                 float wx = w * dx, wy = w * dy, wz = w * dz;
                 float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
                 if (solid_j) {
-                    b0 = s.sd2[(int64_t)j * 2 + 0];
-                    b1 = s.sd2[(int64_t)j * 2 + 1];
+                    b0 = s.sd2[j];
+                    b1 = s.sd2[n + j];
                 }
                 float Txx = as0.x + b0.x, Tyy = as0.y + b0.y, Tzz = as0.z + b0.z;
                 float Txy = as0.w + b0.w, Txz = as1.x + b1.x, Tyz = as1.y + b1.y;
@@ -483,7 +483,7 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
     const int t = threadIdx.x;
     const int c = s.perm[i];
     const int star = st.star ? st.star[c] : 0;
-    const float4 a2 = s.rec[i * 4 + 2];
+    const float4 a2 = s.rec[2 * n + i];
     const float4 p0 = s.pp[i * 2 + 0], p1 = s.pp[i * 2 + 1];
     const bool solid_i = s.tys[i] == 1;
     float aP[3] = {s_acc[A_P0][t], s_acc[A_P1][t], s_acc[A_P2][t]};

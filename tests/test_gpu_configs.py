@@ -129,11 +129,12 @@ def _marginal(state_after, Y0, band):
 
 
 def test_crust_failure_flags():
-    # strong l=2 forcing of a 5000-particle star with an 8 % crust,
+    # strong l=2 forcing of a 2e4-particle star with an 8 % crust (the oracle-sized
+    # version of the 4e6 crust-failure configuration),
     # mu = 0.01 P, Y0 = 1e-3 mu, eps_b = 0.01: yield and damage flags of the
     # FP64 GPU run equal the oracle's, and the mixed run's equal the FP64
     # run's, except for particles within rounding of the yield surface.
-    st, eos, met, prof = I.star_state(5000, seed=7, crust_frac=0.08, mu_over_P=0.01,
+    st, eos, met, prof = I.star_state(20000, seed=7, crust_frac=0.08, mu_over_P=0.01,
                                       Y0_over_mu=1e-3, eps_break=0.01, amp_l0=0.0, amp_l2=0.1)
     dt = I.cfl_dt(st, eos)
     n = 10
