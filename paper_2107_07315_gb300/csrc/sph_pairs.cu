@@ -130,7 +130,8 @@ __device__ __forceinline__ Prep<T> eos_prep(const DevEos &eos, const DevMetric &
 // for the per-particle work (EoS, finalize).
 constexpr int kTB = 128;    // threads per block, mixed precision
 constexpr int kTB64 = 64;   // threads per block, FP64
-constexpr int kRounds = 4;  // phase-1 rounds per block
+constexpr int kRoundsD = 4;  // phase-1 rounds per block, density kernels
+constexpr int kRoundsF = 2;  // phase-1 rounds per block, force kernels
 
 // ------------------------------------------------------------------ density
 template <int LPI, int R>
@@ -614,9 +615,9 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
 
 // Particles per block of each kernel variant (threads / lanes * rounds).
 template <int LPI>
-constexpr int pb_mixed() { return kTB / LPI * kRounds; }
+constexpr int pb_mixed(int rounds) { return kTB / LPI * rounds; }
 template <int LPI>
-constexpr int pb_fp64() { return kTB64 / LPI * kRounds; }
+constexpr int pb_fp64(int rounds) { return kTB64 / LPI * rounds; }
 
 void launch_density(const DevState &st, const Scratch &s, const DevEos &eos, const DevMetric &g,
                     const DevRates &out, int cap, int lanes, int fp64, cudaStream_t stream)
@@ -624,17 +625,17 @@ void launch_density(const DevState &st, const Scratch &s, const DevEos &eos, con
     int64_t n = st.n;
     if (fp64) {
         if (lanes == 4)
-            k_density_fp64<4, kRounds><<<(int)((n + pb_fp64<4>() - 1) / pb_fp64<4>()), kTB64, 0,
+            k_density_fp64<4, kRoundsD><<<(int)((n + pb_fp64<4>(kRoundsD) - 1) / pb_fp64<4>(kRoundsD)), kTB64, 0,
                                          stream>>>(n, st, s, eos, g, out, cap);
         else
-            k_density_fp64<8, kRounds><<<(int)((n + pb_fp64<8>() - 1) / pb_fp64<8>()), kTB64, 0,
+            k_density_fp64<8, kRoundsD><<<(int)((n + pb_fp64<8>(kRoundsD) - 1) / pb_fp64<8>(kRoundsD)), kTB64, 0,
                                          stream>>>(n, st, s, eos, g, out, cap);
     } else {
         if (lanes == 4)
-            k_density_mixed<4, kRounds><<<(int)((n + pb_mixed<4>() - 1) / pb_mixed<4>()), kTB, 0,
+            k_density_mixed<4, kRoundsD><<<(int)((n + pb_mixed<4>(kRoundsD) - 1) / pb_mixed<4>(kRoundsD)), kTB, 0,
                                           stream>>>(n, st, s, eos, g, out, cap);
         else
-            k_density_mixed<8, kRounds><<<(int)((n + pb_mixed<8>() - 1) / pb_mixed<8>()), kTB, 0,
+            k_density_mixed<8, kRoundsD><<<(int)((n + pb_mixed<8>(kRoundsD) - 1) / pb_mixed<8>(kRoundsD)), kTB, 0,
                                           stream>>>(n, st, s, eos, g, out, cap);
     }
 }
@@ -646,17 +647,17 @@ void launch_force(const DevState &st, const Scratch &s, const DevEos &eos, const
     int64_t n = st.n;
     if (fp64) {
         if (lanes == 4)
-            k_force_fp64<4, kRounds><<<(int)((n + pb_fp64<4>() - 1) / pb_fp64<4>()), kTB64, 0,
+            k_force_fp64<4, kRoundsF><<<(int)((n + pb_fp64<4>(kRoundsF) - 1) / pb_fp64<4>(kRoundsF)), kTB64, 0,
                                        stream>>>(n, st, s, eos, mat, g, out, cap);
         else
-            k_force_fp64<8, kRounds><<<(int)((n + pb_fp64<8>() - 1) / pb_fp64<8>()), kTB64, 0,
+            k_force_fp64<8, kRoundsF><<<(int)((n + pb_fp64<8>(kRoundsF) - 1) / pb_fp64<8>(kRoundsF)), kTB64, 0,
                                        stream>>>(n, st, s, eos, mat, g, out, cap);
     } else {
         if (lanes == 4)
-            k_force_mixed<4, kRounds><<<(int)((n + pb_mixed<4>() - 1) / pb_mixed<4>()), kTB, 0,
+            k_force_mixed<4, kRoundsF><<<(int)((n + pb_mixed<4>(kRoundsF) - 1) / pb_mixed<4>(kRoundsF)), kTB, 0,
                                         stream>>>(n, st, s, eos, mat, g, out, cap);
         else
-            k_force_mixed<8, kRounds><<<(int)((n + pb_mixed<8>() - 1) / pb_mixed<8>()), kTB, 0,
+            k_force_mixed<8, kRoundsF><<<(int)((n + pb_mixed<8>(kRoundsF) - 1) / pb_mixed<8>(kRoundsF)), kTB, 0,
                                         stream>>>(n, st, s, eos, mat, g, out, cap);
     }
 }

@@ -30,17 +30,16 @@ __global__ void k_kick_drift(StepState s, DevRates r, double dt)
     s.vp[a] = vx + hdt * ax;
     s.vp[n + a] = vy + hdt * ay;
     s.vp[2 * n + a] = vz + hdt * az;
-    bool solid = s.type[a] == 1;
-    for (int c = 0; c < 6; ++c) {
-        int64_t i = c * n + a;
-        double Sv = s.S[i];
-        if (solid) {
+    // the predicted stress is read for solid particles only (the stress pair
+    // term and the stress rate of fluid particles are zero), so fluid
+    // particles skip it
+    if (s.type[a] == 1) {
+        for (int c = 0; c < 6; ++c) {
+            int64_t i = c * n + a;
             double ds = r.dS[i];
-            Sv += hdt * ds;
+            double Sv = s.S[i] + hdt * ds;
             s.S[i] = Sv;
             s.Sp[i] = Sv + hdt * ds;
-        } else {
-            s.Sp[i] = Sv;
         }
     }
 }
