@@ -167,6 +167,55 @@ def device_state(state: dict, device="cuda"):
     return out
 
 
+# Fields a step changes, first in the packed layout so that one copy moves them.
+STEP_KEYS = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "S", "flags")
+
+
+def device_state_packed(state: dict, device="cuda"):
+    """Like device_state, but every field is a view into one device buffer.
+
+    The fields a step changes (STEP_KEYS) come first, each at a 256-byte
+    aligned offset, so a caller that keeps the state on the host can move a
+    step's inputs and results with one copy each way.  Returns (fields,
+    buffer, step_bytes): the field views (as device_state), the uint8 buffer
+    and the length of its leading step part.
+    """
+    import torch
+
+    arrays = {}
+    for k in PARTICLE_KEYS:
+        v = state.get(k)
+        if v is None:
+            continue
+        a = np.ascontiguousarray(v)
+        if k in ("type", "flags"):
+            a = a.astype(np.uint8)
+        elif k == "star":
+            a = a.astype(np.int32)
+        else:
+            a = a.astype(np.float64)
+        arrays[k] = a
+    order = [k for k in STEP_KEYS if k in arrays] + [k for k in PARTICLE_KEYS
+                                                      if k in arrays and k not in STEP_KEYS]
+    offs, pos = {}, 0
+    for k in order:
+        offs[k] = pos
+        pos = (pos + arrays[k].nbytes + 255) // 256 * 256
+    last = [k for k in order if k in STEP_KEYS][-1]
+    step_bytes = offs[last] + arrays[last].nbytes
+    host = np.zeros(max(pos, 1), np.uint8)
+    for k in order:
+        host[offs[k]:offs[k] + arrays[k].nbytes] = arrays[k].reshape(-1).view(np.uint8)
+    buf = torch.from_numpy(host).to(device)
+    dtypes = {np.dtype(np.float64): torch.float64, np.dtype(np.uint8): torch.uint8,
+              np.dtype(np.int32): torch.int32}
+    fields = {k: None for k in PARTICLE_KEYS}
+    for k in order:
+        a = arrays[k]
+        fields[k] = buf[offs[k]:offs[k] + a.nbytes].view(dtypes[a.dtype]).view(a.shape)
+    return fields, buf, step_bytes
+
+
 def alloc_rates(n: int, device="cuda"):
     import torch
 
