@@ -1,0 +1,32 @@
+"""Host-side checks of the binding helpers (no GPU needed)."""
+import numpy as np
+
+from paper_2107_07315_gb300 import inputs as I
+from paper_2107_07315_gb300 import sph
+
+
+def test_packed_state_layout():
+    # every field is an aligned, contiguous view with the caller's values, and
+    # the fields a step changes form one leading byte range
+    st, _ = I.random_state(777, seed=5, vel=0.2, stress=0.05)
+    f, buf, step_bytes = sph.device_state_packed(st, device="cpu")
+    base = buf.data_ptr()
+    ends = []
+    for k in sph.PARTICLE_KEYS:
+        if st.get(k) is None:
+            assert f[k] is None
+            continue
+        a = np.asarray(st[k])
+        t = f[k]
+        assert t.is_contiguous() and tuple(t.shape) == a.shape, k
+        off = t.data_ptr() - base
+        assert off % 256 == 0, k
+        assert np.array_equal(t.numpy(), a.astype(t.numpy().dtype)), k
+        ends.append((k, off, off + t.numel() * t.element_size()))
+    step = [e for e in ends if e[0] in sph.STEP_KEYS]
+    rest = [e for e in ends if e[0] not in sph.STEP_KEYS]
+    assert max(e[2] for e in step) == step_bytes
+    assert all(r[1] >= step_bytes for r in rest)
+    # views alias the buffer: a write through the buffer shows in the field
+    buf[f["u"].data_ptr() - base:f["u"].data_ptr() - base + 8] = 0
+    assert f["u"][0].item() == 0.0
