@@ -96,6 +96,21 @@ typedef struct {
     const double *r_max, *alpha, *dalpha, *psi4, *dpsi4, *M, *center;
 } sph_metric;
 
+/* External field of the particle relaxation (Sec. II.A), host tables.  The
+ * relaxation confines the particles in phi_eff = -K Gamma rho_t^(Gamma-1) /
+ * (Gamma-1) of a target density profile rho_t(r); g holds the radial
+ * component of g_eff = -grad phi_eff (negative = inward) per star on nr
+ * uniform nodes over [0, r_max[s]] around center[3*s..], zero beyond r_max.
+ * Readings of passages the paper leaves open: beyond r_wall[s] a wall adds
+ * -k_wall (r - r_wall) along r_hat ("potential walls"), and every particle
+ * feels -damping v, which lets the particles settle into equilibrium.
+ * kind 0 switches the field off. */
+typedef struct {
+    int32_t kind, nstars, nr, reserved;
+    const double *r_max, *g, *center, *r_wall;
+    double k_wall, damping;
+} sph_external;
+
 /* Rates and derived fields (device, caller order), all length n unless
  * noted: acceleration a (Eq. solid2 plus the background force of Sec. I.C),
  * du/dt (Eq. solid3), continuity rate (Eq. solid1 with the computational
@@ -190,6 +205,21 @@ sph_status sph_get_state(sph_ctx *ctx, void *host_buf, int64_t bytes);
 sph_status sph_set_state(sph_ctx *ctx, const void *host_buf, int64_t bytes);
 
 /* Release the context and its device memory (the caller's buffers stay). */
+/* Switch the external relaxation field on (kind 1) or off (NULL or kind 0)
+ * for later right-hand sides and steps (Sec. II.A).  The tables are copied
+ * into device memory owned by the context (each call allocates new copies,
+ * freed by sph_free).  Errors: SPH_ERR_ARG (star count differs from the
+ * context's, nr < 2, NULL table, non-finite or negative values). */
+sph_status sph_set_external(sph_ctx *ctx, const sph_external *ext);
+
+/* Modification step after a relaxation (Sec. II.A): replace the context's
+ * equation of state by eos (the star's, per star), evaluate the density of
+ * the current state (a right-hand side without the external field, which
+ * this call switches off) and set u = K rho^(Gamma-1)/(Gamma-1) for every
+ * particle.  Positions, velocities and h are kept.  Errors: SPH_ERR_ARG
+ * (star count, K <= 0, Gamma <= 1), SPH_ERR_CUDA. */
+sph_status sph_relax_finish(sph_ctx *ctx, const sph_eos *eos);
+
 void sph_free(sph_ctx *ctx);
 
 /* Neighbour lists without a context and without any device allocation, for

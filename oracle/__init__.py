@@ -64,6 +64,12 @@ class _Metric(C.Structure):
                 ("dpsi4", _d), ("M", _d), ("center", _d)]
 
 
+class _External(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nstars", C.c_int32), ("nr", C.c_int32),
+                ("r_max", _d), ("g", _d), ("center", _d), ("r_wall", _d),
+                ("k_wall", C.c_double), ("damping", C.c_double)]
+
+
 class _Scales(C.Structure):
     _fields_ = [(k, _d) for k in ("a", "du", "drho", "D", "eps", "dS")]
 
@@ -108,6 +114,8 @@ def lib():
                                            C.c_double, _d]
             L.ora_eos_eval.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int,
                                        _d, _d, _d, _d]
+            L.ora_external_accel.argtypes = [C.POINTER(_External), C.c_int, C.c_double,
+                                             C.c_double, C.c_double, _d, _d, _d]
             L.ora_num_threads.restype = C.c_int
             L.ora_set_threads.argtypes = [C.c_int]
             _lib = L
@@ -166,6 +174,30 @@ def _cmetric(g, keep: list):
                    ("r_max", "alpha", "dalpha", "psi4", "dpsi4", "M", "center")])
 
 
+def _cexternal(e, keep: list):
+    """ctypes view of an external relaxation field dict (None: no field)."""
+    if e is None or int(e.get("kind", 1)) == 0:
+        return None
+    arrs = {k: np.ascontiguousarray(e[k], dtype=np.float64).ravel()
+            for k in ("r_max", "g", "center", "r_wall")}
+    keep.append(arrs)
+    return _External(1, len(arrs["r_max"]), int(e["nr"]), _p(arrs["r_max"]), _p(arrs["g"]),
+                     _p(arrs["center"]), _p(arrs["r_wall"]), float(e["k_wall"]),
+                     float(e["damping"]))
+
+
+def external_accel(external: dict, star: int, x: float, y: float, z: float, v) -> tuple:
+    """External relaxation acceleration (vector, magnitude) at one point."""
+    keep: list = []
+    ce = _cexternal(external, keep)
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    acc = np.zeros(3, np.float64)
+    mag = np.zeros(1, np.float64)
+    lib().ora_external_accel(C.byref(ce) if ce is not None else None, int(star), float(x),
+                             float(y), float(z), _p(vv), _p(acc), _p(mag))
+    return acc, float(mag[0])
+
+
 _RATE_KEYS = ("ax", "ay", "az", "dudt", "drhodt", "rho", "P", "D", "cs")
 
 
@@ -192,7 +224,7 @@ def num_threads() -> int:
 
 
 def rhs(state: dict, eos: dict, material: dict, metric=None, subset=None,
-        v=None, S=None, scales: bool = False) -> dict:
+        v=None, S=None, scales: bool = False, external=None) -> dict:
     """Rates of the full RHS (Eqs. solid1-solid6 + background force).
 
     ``subset``: optional int64 array of particle ids; only their rates are
@@ -215,6 +247,7 @@ def rhs(state: dict, eos: dict, material: dict, metric=None, subset=None,
     ce = _ceos(eos, keep)
     cm = _cmat(material)
     cg = _cmetric(metric, keep)
+    cx = _cexternal(external, keep)
     r = _alloc_rates(n)
     cr = _crates(r)
     if subset is not None:
@@ -227,7 +260,8 @@ def rhs(state: dict, eos: dict, material: dict, metric=None, subset=None,
         sc_arr = {k: np.zeros(n, np.float64) for k in ("a", "du", "drho", "D", "eps", "dS")}
         sc = _Scales(*[_p(sc_arr[k]) for k in ("a", "du", "drho", "D", "eps", "dS")])
     rc = L.ora_rhs(C.byref(cs), _p(vx), _p(vy), _p(vz), _p(Sarr), C.byref(ce), C.byref(cm),
-                   C.byref(cg) if cg is not None else None, sp, C.c_int64(ns), C.byref(cr),
+                   C.byref(cg) if cg is not None else None,
+                   C.byref(cx) if cx is not None else None, sp, C.c_int64(ns), C.byref(cr),
                    C.byref(sc) if sc is not None else None)
     if rc != 0:
         raise MemoryError("oracle rhs failed")
@@ -257,7 +291,7 @@ def neighbors(state: dict, subset=None):
 
 
 def step(state: dict, eos: dict, material: dict, metric, dt: float, nsteps: int,
-         h_nmin: int = 0, h_nmax: int = 0, rates=None):
+         h_nmin: int = 0, h_nmax: int = 0, rates=None, external=None):
     """Advance ``nsteps`` leapfrog steps; returns (new_state, rates).
 
     ``rates`` from a previous call continue the scheme exactly; when None the
@@ -272,6 +306,7 @@ def step(state: dict, eos: dict, material: dict, metric, dt: float, nsteps: int,
     ce = _ceos(eos, keep)
     cm = _cmat(material)
     cg = _cmetric(metric, keep)
+    cx = _cexternal(external, keep)
     if rates is None:
         r, have = _alloc_rates(n), 0
     else:
@@ -279,7 +314,8 @@ def step(state: dict, eos: dict, material: dict, metric, dt: float, nsteps: int,
         have = 1
     cr = _crates(r)
     rc = L.ora_step(C.byref(cs), C.byref(ce), C.byref(cm),
-                    C.byref(cg) if cg is not None else None, C.c_double(dt),
+                    C.byref(cg) if cg is not None else None,
+                    C.byref(cx) if cx is not None else None, C.c_double(dt),
                     C.c_int32(nsteps), C.c_int32(h_nmin), C.c_int32(h_nmax), C.c_int32(have),
                     C.byref(cr))
     if rc != 0:

@@ -70,6 +70,22 @@ typedef struct {
     const double *center; /* [3*nstars] */
 } ora_metric;
 
+/* External field of the relaxation (Sec. II.A "particle relaxation"):     */
+/* g_eff = -grad phi_eff with phi_eff = -K Gamma rho_t^(Gamma-1)/(Gamma-1)   */
+/* for a target profile rho_t(r), tabulated as its radial component g on     */
+/* uniform nodes 0..r_max (0 beyond).  Readings (the paper names walls and   */
+/* leaves the relaxation's dissipation open): a wall a = -k_wall (r - r_wall) */
+/* r_hat beyond r_wall, and velocity damping a = -damping v.                 */
+typedef struct {
+    int32_t kind; /* 0: none ; 1: radial table */
+    int32_t nstars, nr;
+    const double *r_max;  /* [nstars] */
+    const double *g;      /* [nstars*nr] radial component (negative = inward) */
+    const double *center; /* [3*nstars] */
+    const double *r_wall; /* [nstars] */
+    double k_wall, damping;
+} ora_external;
+
 typedef struct {
     double *ax, *ay, *az, *dudt, *drhodt, *rho, *P, *D, *cs;
     double *deps, *dR, *dS; /* 6n, 3n, 6n component-major */
@@ -399,10 +415,40 @@ static double art_visc(const ora_material *mat, double hab, double vdx, double r
  * the viscous and elastic parts are added in Newtonian form (Sec. III:
  * Newtonian elastodynamics combined with relativistic hydrodynamics).
  */
+/* External acceleration of particle a with velocity v (added to the RHS    */
+/* acceleration); *mag receives the sum of the magnitudes of its parts.      */
+void ora_external_accel(const ora_external *e, int st, double x, double y, double z,
+                        const double *v, double *acc, double *mag)
+{
+    acc[0] = acc[1] = acc[2] = 0.0;
+    *mag = 0.0;
+    if (!e || e->kind != 1) return;
+    double c[3] = {x - e->center[3 * st + 0], y - e->center[3 * st + 1],
+                   z - e->center[3 * st + 2]};
+    double r = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    double gr = 0.0;
+    double rmax = e->r_max[st];
+    if (r <= rmax) {
+        double dr = rmax / (double)(e->nr - 1);
+        double t = r / dr;
+        int i = (int)floor(t);
+        if (i > e->nr - 2) i = e->nr - 2;
+        if (i < 0) i = 0;
+        double f = t - (double)i;
+        const double *tab = e->g + (int64_t)st * e->nr;
+        gr = tab[i] + f * (tab[i + 1] - tab[i]);
+    }
+    if (r > e->r_wall[st]) gr -= e->k_wall * (r - e->r_wall[st]);
+    if (r > 0.0)
+        for (int k = 0; k < 3; ++k) acc[k] = gr * c[k] / r;
+    for (int k = 0; k < 3; ++k) acc[k] -= e->damping * v[k];
+    *mag = fabs(gr) + e->damping * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
 int ora_rhs(const ora_state *s, const double *vx, const double *vy, const double *vz,
             const double *S, const ora_eos *eos, const ora_material *mat,
-            const ora_metric *g, const int64_t *list, int64_t nlist, ora_rates *out,
-            ora_scales *scl)
+            const ora_metric *g, const ora_external *ext, const int64_t *list, int64_t nlist,
+            ora_rates *out, ora_scales *scl)
 {
     int64_t n = s->n;
     int64_t cnt = list ? nlist : n;
@@ -586,6 +632,12 @@ int ora_rhs(const ora_state *s, const double *vx, const double *vy, const double
         } else {
             for (int i = 0; i < 3; ++i) acc[i] = aP[i] + aV[i] + aS[i];
         }
+        if (ext && ext->kind == 1) {
+            double ea[3], em;
+            ora_external_accel(ext, star_of(s, a), s->x[a], s->y[a], s->z[a], va, ea, &em);
+            for (int i = 0; i < 3; ++i) acc[i] += ea[i];
+            if (scl) scl->a[a] += em;
+        }
         out->ax[a] = acc[0];
         out->ay[a] = acc[1];
         out->az[a] = acc[2];
@@ -727,12 +779,12 @@ void ora_totals(const ora_state *s, const int32_t *ncount, double *out)
 /* have_rates == 0 they are first evaluated at the current state.            */
 /* ------------------------------------------------------------------------ */
 int ora_step(ora_state *s, const ora_eos *eos, const ora_material *mat, const ora_metric *g,
-             double dt, int32_t nsteps, int32_t h_nmin, int32_t h_nmax, int32_t have_rates,
-             ora_rates *r)
+             const ora_external *ext, double dt, int32_t nsteps, int32_t h_nmin, int32_t h_nmax,
+             int32_t have_rates, ora_rates *r)
 {
     int64_t n = s->n;
     if (!have_rates) {
-        if (ora_rhs(s, s->vx, s->vy, s->vz, s->S, eos, mat, g, NULL, 0, r, NULL)) return 1;
+        if (ora_rhs(s, s->vx, s->vy, s->vz, s->S, eos, mat, g, ext, NULL, 0, r, NULL)) return 1;
     }
     double *vp = (double *)malloc(sizeof(double) * (size_t)(3 * n + 1));
     double *Sp = (double *)malloc(sizeof(double) * (size_t)(6 * n + 1));
@@ -756,7 +808,7 @@ int ora_step(ora_state *s, const ora_eos *eos, const ora_material *mat, const or
                 Sp[i] = s->S[i] + hdt * r->dS[i];
             }
         }
-        if (ora_rhs(s, vp, vp + n, vp + 2 * n, Sp, eos, mat, g, NULL, 0, r, NULL)) {
+        if (ora_rhs(s, vp, vp + n, vp + 2 * n, Sp, eos, mat, g, ext, NULL, 0, r, NULL)) {
             free(vp); free(Sp); return 1;
         }
         for (int64_t a = 0; a < n; ++a) {

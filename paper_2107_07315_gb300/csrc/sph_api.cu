@@ -700,6 +700,89 @@ sph_status sph_neighbors(sph_ctx *c, int64_t *offsets, int32_t *idx, int64_t cap
     return SPH_OK;
 }
 
+sph_status sph_set_external(sph_ctx *c, const sph_external *e)
+{
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    if (!e || e->kind == 0) {
+        c->met.ext_kind = 0;
+        drop_graph(c);
+        return SPH_OK;
+    }
+    if (e->kind != 1) return fail(SPH_ERR_ARG, "external kind must be 0 or 1");
+    if (e->nstars != c->nstars) return fail(SPH_ERR_ARG, "external and eos star counts differ");
+    if (e->nr < 2 || !e->r_max || !e->g || !e->center || !e->r_wall)
+        return fail(SPH_ERR_ARG, "external table needs nr >= 2 and r_max, g, center, r_wall");
+    if (!(e->k_wall >= 0.0) || !(e->damping >= 0.0) || !std::isfinite(e->k_wall) ||
+        !std::isfinite(e->damping))
+        return fail(SPH_ERR_ARG, "k_wall and damping must be finite and >= 0");
+    const int ns = e->nstars, nr = e->nr;
+    for (int s = 0; s < ns; ++s) {
+        if (!(e->r_max[s] > 0.0) || !std::isfinite(e->r_max[s]) || !std::isfinite(e->r_wall[s]))
+            return fail(SPH_ERR_ARG, "star %d: need finite r_max > 0 and r_wall", s);
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(e->center[3 * s + k])) return fail(SPH_ERR_ARG, "non-finite center");
+    }
+    std::vector<float> gf((size_t)ns * nr);
+    for (size_t k = 0; k < gf.size(); ++k) {
+        if (!std::isfinite(e->g[k])) return fail(SPH_ERR_ARG, "non-finite external table");
+        gf[k] = (float)e->g[k];
+    }
+    double *d_g, *d_rmax, *d_center, *d_rwall;
+    float *d_gf;
+    STATUS_TRY(c->alloc(&d_g, gf.size()));
+    STATUS_TRY(c->alloc(&d_gf, gf.size()));
+    STATUS_TRY(c->alloc(&d_rmax, ns));
+    STATUS_TRY(c->alloc(&d_center, 3 * ns));
+    STATUS_TRY(c->alloc(&d_rwall, ns));
+    CUDA_TRY(cudaMemcpy(d_g, e->g, gf.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_gf, gf.data(), gf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_rmax, e->r_max, ns * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_center, e->center, 3 * ns * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_rwall, e->r_wall, ns * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->met.ext_kind = 1;
+    c->met.ext_nr = nr;
+    c->met.ext_g = d_g;
+    c->met.ext_gf = d_gf;
+    c->met.ext_rmax = d_rmax;
+    c->met.ext_center = d_center;
+    c->met.ext_rwall = d_rwall;
+    c->met.k_wall = e->k_wall;
+    c->met.damping = e->damping;
+    drop_graph(c);
+    c->have_rates = 0;  // the field changes the accelerations
+    return SPH_OK;
+}
+
+sph_status sph_relax_finish(sph_ctx *c, const sph_eos *eos)
+{
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    if (!eos || eos->nstars != c->nstars || !eos->K || !eos->Gamma)
+        return fail(SPH_ERR_ARG, "eos must give K and Gamma for each of the %d stars", c->nstars);
+    for (int s = 0; s < eos->nstars; ++s) {
+        if (!(eos->Gamma[s] > 1.0) || !(eos->K[s] > 0.0) || !std::isfinite(eos->Gamma[s]) ||
+            !std::isfinite(eos->K[s]))
+            return fail(SPH_ERR_ARG, "star %d: need K > 0 and Gamma > 1", s);
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaMemcpy(c->d_K, eos->K, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_Gamma, eos->Gamma, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
+    c->met.ext_kind = 0;
+    drop_graph(c);
+    if (c->n > 0) {
+        // density of the relaxed state, then u from the new equation of state
+        int timing = c->timing;
+        c->timing = 0;
+        DevState st = state_of(c, c->P.vx, c->P.vy, c->P.vz, c->P.S);
+        enqueue_rhs(c, st, c->r, false, nullptr);
+        c->timing = timing;
+        launch_set_u_from_eos(step_state_of(c), c->r, eos_of(c), c->stream);
+        CUDA_TRY(cudaGetLastError());
+    }
+    c->have_rates = 0;  // the next step starts from rates of the modified state
+    return SPH_OK;
+}
+
 sph_status sph_totals(sph_ctx *c, double out[16])
 {
     if (!c || !out) return fail(SPH_ERR_ARG, "null argument");

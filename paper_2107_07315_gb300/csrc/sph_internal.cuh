@@ -87,11 +87,20 @@ struct DevMaterial {
     int jaumann, yield_mode, break_stress, break_zero_S;
 };
 
+// Background fields of the right-hand side: the fixed metric (Sec. I.C) and
+// the external field of the relaxation (Sec. II.A).
 struct DevMetric {
     int kind, nstars, nr, pressure_form;
     const double *r_max, *M, *center;
     const double *tab;   // [nstars][nr][4]: alpha, dalpha, psi4, dpsi4
     const float *tabf;   // FP32 copy
+    // external field: radial g_eff on nodes 0..ext_rmax (0 beyond), a wall
+    // -k_wall (r - r_wall) beyond r_wall, damping -damping v; ext_kind 0: off
+    int ext_kind, ext_nr;
+    const double *ext_rmax, *ext_center, *ext_rwall;
+    const double *ext_g;  // [nstars][ext_nr]
+    const float *ext_gf;  // FP32 copy
+    double k_wall, damping;
 };
 
 struct DevRates {
@@ -191,6 +200,11 @@ struct StepState {
     double *mu, *Y0, *eps_break;
     double *vp, *Sp;  // predicted velocity (3n) and stress (6n)
 };
+
+// Modification step after a relaxation (Sec. II.A): u = K rho^(Gamma-1)/(Gamma-1)
+// from the density of the last right-hand side, per star's EoS.
+void launch_set_u_from_eos(const StepState &s, const DevRates &r, const DevEos &eos,
+                           cudaStream_t stream);
 
 void launch_kick_drift(const StepState &s, const DevRates &r, double dt, cudaStream_t st);
 void launch_kick_return(const StepState &s, const DevRates &r, const DevEos &eos,

@@ -287,6 +287,43 @@ k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRa
     out.ncount[c] = s.ncnt[i];
 }
 
+// External field of the relaxation (Sec. II.A) at a particle with velocity v:
+// g_eff(r) r_hat from the table, the wall beyond r_wall, and -damping v.
+template <typename T>
+__device__ __forceinline__ void external_at(const DevMetric &g, int s, double x, double y,
+                                            double z, T vx, T vy, T vz, T acc[3])
+{
+    T c[3] = {(T)(x - g.ext_center[3 * s + 0]), (T)(y - g.ext_center[3 * s + 1]),
+              (T)(z - g.ext_center[3 * s + 2])};
+    T r = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    T gr = (T)0;
+    T rmax = (T)g.ext_rmax[s];
+    if (r <= rmax) {
+        T dr = rmax / (T)(g.ext_nr - 1);
+        T t = r / dr;
+        int i = (int)floor(t);
+        i = max(0, min(i, g.ext_nr - 2));
+        T f = t - (T)i;
+        int64_t o = (int64_t)s * g.ext_nr + i;
+        T g0, g1;
+        if (sizeof(T) == 8) {
+            g0 = (T)g.ext_g[o];
+            g1 = (T)g.ext_g[o + 1];
+        } else {
+            g0 = (T)g.ext_gf[o];
+            g1 = (T)g.ext_gf[o + 1];
+        }
+        gr = g0 + f * (g1 - g0);
+    }
+    T rw = (T)g.ext_rwall[s];
+    if (r > rw) gr -= (T)g.k_wall * (r - rw);
+    T inv = r > (T)0 ? (T)1 / r : (T)0;
+    T d = (T)g.damping;
+    acc[0] = gr * c[0] * inv - d * vx;
+    acc[1] = gr * c[1] * inv - d * vy;
+    acc[2] = gr * c[2] * inv - d * vz;
+}
+
 // -------------------------------------------------------------- finalize
 // Strain rate, rotation rate, stress rate (Eq. solid4), elastic work
 // (Eq. solid3) and acceleration, from the reduced pair sums of particle i.
@@ -348,6 +385,11 @@ __device__ __forceinline__ void finalize(int64_t i, int c, int64_t N, const DevS
         }
     } else {
         for (int k = 0; k < 3; ++k) acc[k] = aP[k] + aX[k];
+    }
+    if (g.ext_kind == 1) {
+        T e[3];
+        external_at<T>(g, star, x, y, z, vx, vy, vz, e);
+        for (int k = 0; k < 3; ++k) acc[k] += e[k];
     }
     out.ax[c] = (double)acc[0];
     out.ay[c] = (double)acc[1];

@@ -11,6 +11,18 @@ namespace sph {
 
 namespace {
 
+// Modification step after a relaxation (Sec. II.A): the specific internal
+// energy of the polytrope, u = K rho^(Gamma-1)/(Gamma-1), for the density of
+// the last right-hand side.
+__global__ void k_set_u(StepState s, DevRates r, DevEos eos)
+{
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    const int star = s.star ? s.star[a] : 0;
+    const double K = eos.K[star], G = eos.Gamma[star];
+    s.u[a] = K * pow(r.rho[a], G - 1.0) / (G - 1.0);
+}
+
 // Half kick, drift, and the predicted velocity/stress used by the RHS.
 __global__ void k_kick_drift(StepState s, DevRates r, double dt)
 {
@@ -262,6 +274,13 @@ __global__ void k_export_fill(const int32_t *perm, const int32_t *nbr, const int
 }
 
 }  // namespace
+
+void launch_set_u_from_eos(const StepState &s, const DevRates &r, const DevEos &eos,
+                           cudaStream_t stream)
+{
+    if (s.n == 0) return;
+    k_set_u<<<(int)((s.n + 255) / 256), 256, 0, stream>>>(s, r, eos);
+}
 
 void launch_kick_drift(const StepState &s, const DevRates &r, double dt, cudaStream_t st)
 {

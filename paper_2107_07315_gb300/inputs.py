@@ -362,6 +362,75 @@ def star_state(N: int, Gamma: float = 2.0, seed: int = 1, crust_frac: float = 0.
     return st, eos, metric, prof
 
 
+# ---------------------------------------------------------------------------
+# Relaxation in an external potential (Sec. II.A)
+# ---------------------------------------------------------------------------
+def relax_eos(prof: TovProfile, Gamma_r: float = 1.01) -> dict:
+    """Relaxation EoS: Gamma ~ 1.01 (nearly uniform sound speed), K chosen to
+    keep the star's central pressure, K_r = K rho_c^(Gamma - Gamma_r)."""
+    K_r = prof.K * prof.rho_c ** (prof.Gamma - Gamma_r)
+    return dict(K=np.array([K_r]), Gamma=np.array([Gamma_r]))
+
+
+def relax_external(profs, centers, eos_r: dict, nr: int = 4096, wall_factor: float = 1.0,
+                   k_wall=None, damping: float = 0.0, rho_floor: float = 0.01) -> dict:
+    """External field of the relaxation for each star.
+
+    Target profile: the coordinate (SPH) density of the star, rho_t = rho psi^6
+    on the isotropic radius; phi_eff = -K Gamma rho_t^(Gamma-1)/(Gamma-1) with
+    the relaxation EoS, tabulated on nr uniform nodes over [0, rbar_s] and
+    differentiated by second-order differences: g = -d phi_eff/dr (negative =
+    inward).  rho_t is floored at rho_floor * rho_t(0): with Gamma ~ 1 the
+    equilibrium force K Gamma rho^(Gamma-2) grad rho diverges like 1/(R - r)
+    at the surface, which no smoothed density resolves.  Wall at
+    wall_factor * rbar_s with stiffness k_wall (default 10 max|g| / rbar_s);
+    damping in 1/time.
+    """
+    ns = len(profs)
+    K_r = np.asarray(eos_r["K"], np.float64)
+    G_r = np.asarray(eos_r["Gamma"], np.float64)
+    out = dict(kind=1, nr=nr, r_max=np.zeros(ns), g=np.zeros((ns, nr)),
+               center=np.asarray(centers, dtype=np.float64).reshape(ns, 3),
+               r_wall=np.zeros(ns), k_wall=0.0, damping=float(damping))
+    kmax = 0.0
+    for s, p in enumerate(profs):
+        grid = np.linspace(0.0, p.rbar_s, nr)
+        rho_t = np.interp(grid, p.rbar, p.rho * p.psi4 ** 1.5)
+        rho_t = np.maximum(rho_t, rho_floor * rho_t[0])
+        k, gm = K_r[min(s, len(K_r) - 1)], G_r[min(s, len(G_r) - 1)]
+        phi = -k * gm * rho_t ** (gm - 1.0) / (gm - 1.0)
+        out["g"][s] = -np.gradient(phi, grid, edge_order=2)
+        out["r_max"][s] = p.rbar_s
+        out["r_wall"][s] = wall_factor * p.rbar_s
+        kmax = max(kmax, 10.0 * np.abs(out["g"][s]).max() / p.rbar_s)
+    out["k_wall"] = float(kmax if k_wall is None else k_wall)
+    return out
+
+
+def relax_state(N: int, seed: int = 1, Gamma_r: float = 1.01, jitter: float = 0.15,
+                damping_per_crossing: float = 2.0, M: float = 1.4, R_km: float = 12.0,
+                nr: int = 4096, prof: TovProfile | None = None):
+    """Start of a relaxation: the star of star_state (all fluid, at rest) with
+    positions jittered by `jitter` times the local h, the relaxation EoS and
+    its external field.  Returns (state, eos_r, external, eos_star, prof);
+    damping = damping_per_crossing * c_s / R."""
+    st, eos, _, prof = star_state(N, seed=seed, crust_frac=0.0, amp_l0=0.0, amp_l2=0.0, M=M,
+                                  R_km=R_km, nr=nr, prof=prof)
+    rng = np.random.default_rng(seed + 1000)
+    d = rng.normal(size=(3, N)) * (jitter * st["h"] / math.sqrt(3.0))
+    st["x"] = st["x"] + d[0]
+    st["y"] = st["y"] + d[1]
+    st["z"] = st["z"] + d[2]
+    eos_r = relax_eos(prof, Gamma_r)
+    K_r, G_r = float(eos_r["K"][0]), float(eos_r["Gamma"][0])
+    rho_c = prof.rho_c
+    st["u"][:] = K_r * rho_c ** (G_r - 1.0) / (G_r - 1.0)
+    cs = math.sqrt(G_r * K_r * rho_c ** (G_r - 1.0))
+    ext = relax_external([prof], [(0.0, 0.0, 0.0)], eos_r, nr=nr,
+                         damping=damping_per_crossing * cs / prof.rbar_s)
+    return st, eos_r, ext, eos, prof
+
+
 def cfl_dt(state: dict, eos: dict, C: float = 0.3) -> float:
     """dt = C min_a h_a/(c_a + |v_a|) with the initial-profile sound speed."""
     # sound speed from u: c^2 = Gamma K rho^(Gamma-1) = (Gamma-1) Gamma u (polytrope)

@@ -26,7 +26,8 @@ STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
 # Every symbol include/sph.h declares.
 EXPORTS = ("sph_init", "sph_rhs", "sph_step", "sph_sync", "sph_neighbors", "sph_totals",
            "sph_stats", "sph_timing", "sph_timing_read", "sph_state_size", "sph_get_state",
-           "sph_set_state", "sph_free", "sph_last_error", "sph_neighbors_noalloc")
+           "sph_set_state", "sph_free", "sph_last_error", "sph_neighbors_noalloc",
+           "sph_set_external", "sph_relax_finish")
 
 
 class SphError(RuntimeError):
@@ -61,6 +62,12 @@ class sph_metric(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nstars", C.c_int32), ("nr", C.c_int32),
                 ("pressure_form", C.c_int32)] + [(k, _d) for k in (
                     "r_max", "alpha", "dalpha", "psi4", "dpsi4", "M", "center")]
+
+
+class sph_external(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nstars", C.c_int32), ("nr", C.c_int32),
+                ("reserved", C.c_int32)] + [(k, _d) for k in ("r_max", "g", "center", "r_wall")] + [
+        ("k_wall", C.c_double), ("damping", C.c_double)]
 
 
 class sph_rates(C.Structure):
@@ -102,6 +109,8 @@ def lib():
         L.sph_free.argtypes = [vp]
         L.sph_free.restype = None
         L.sph_neighbors_noalloc.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, C.c_int64, vp]
+        L.sph_set_external.argtypes = [vp, C.POINTER(sph_external)]
+        L.sph_relax_finish.argtypes = [vp, C.POINTER(sph_eos)]
         L.sph_last_error.restype = C.c_char_p
         for f in EXPORTS:
             if f not in ("sph_free", "sph_last_error"):
@@ -282,6 +291,26 @@ def sph_rhs(ctx: SphCtx, rates: dict) -> None:
 
 def sph_step(ctx: SphCtx, dt: float, nsteps: int = 1) -> None:
     _check(lib().sph_step(ctx.handle, float(dt), int(nsteps)), "sph_step")
+
+
+def sph_set_external(ctx: SphCtx, external) -> None:
+    """External relaxation field (dict with nr, r_max, g, center, r_wall, k_wall,
+    damping; see inputs.relax_external), or None to switch it off."""
+    if external is None or int(external.get("kind", 1)) == 0:
+        _check(lib().sph_set_external(ctx.handle, None), "sph_set_external")
+        return
+    arrs = {k: _f64(external[k]) for k in ("r_max", "g", "center", "r_wall")}
+    x = sph_external(1, len(arrs["r_max"]), int(external["nr"]), 0,
+                     *[arrs[k].ctypes.data_as(_d) for k in ("r_max", "g", "center", "r_wall")],
+                     float(external["k_wall"]), float(external["damping"]))
+    _check(lib().sph_set_external(ctx.handle, C.byref(x)), "sph_set_external")
+
+
+def sph_relax_finish(ctx: SphCtx, eos: dict) -> None:
+    """Modification step after a relaxation: new EoS, u from the density."""
+    K, G = _f64(eos["K"]), _f64(eos["Gamma"])
+    e = sph_eos(len(K), K.ctypes.data_as(_d), G.ctypes.data_as(_d))
+    _check(lib().sph_relax_finish(ctx.handle, C.byref(e)), "sph_relax_finish")
 
 
 def sph_sync(ctx: SphCtx) -> None:

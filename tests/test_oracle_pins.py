@@ -474,3 +474,68 @@ def test_star_generator_targets():
     p = I.tov_solve(K, 2.0, rc)
     assert p.M == pytest.approx(1.4, rel=1e-9)
     assert p.R / I.KM == pytest.approx(12.0, rel=1e-9)
+
+
+# ---------------------------------------------------------------- relaxation
+# External field of the particle relaxation (Sec. II.A).
+
+def _linear_external(c=0.8, r_max=2.0, nr=5, r_wall=1.5, k_wall=3.0, damping=0.7):
+    grid = np.linspace(0.0, r_max, nr)
+    return dict(kind=1, nr=nr, r_max=np.array([r_max]), g=(-c * grid)[None, :],
+                center=np.array([[1.0, 2.0, 3.0]]), r_wall=np.array([r_wall]),
+                k_wall=k_wall, damping=damping)
+
+
+def test_external_accel_closed_form():
+    # a linear table g(r) = -c r is interpolated exactly: inside the wall the
+    # acceleration is -c r r_hat - damping v, beyond it the wall adds
+    # -k_wall (r - r_wall) r_hat, beyond r_max only the wall acts
+    c, kw, dmp, rw, rmax = 0.8, 3.0, 0.7, 1.5, 2.0
+    e = _linear_external(c=c, r_max=rmax, r_wall=rw, k_wall=kw, damping=dmp)
+    rng = np.random.default_rng(4)
+    for r in (0.0, 0.3, 1.2, 1.7, 2.5):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        x = np.array([1.0, 2.0, 3.0]) + r * d
+        v = rng.normal(size=3)
+        acc, mag = oracle.external_accel(e, 0, *x, v)
+        gr = (-c * r if r <= rmax else 0.0) - (kw * (r - rw) if r > rw else 0.0)
+        want = gr * d - dmp * v
+        assert np.allclose(acc, want, rtol=1e-13, atol=1e-13), (r, acc, want)
+        assert abs(mag - (abs(gr) + dmp * np.linalg.norm(v))) < 1e-13
+
+
+def test_relax_potential_balances_pressure():
+    # g_eff = -grad phi_eff with phi_eff = -K Gamma rho^(Gamma-1)/(Gamma-1)
+    # balances the pressure force of the relaxation EoS exactly:
+    # g = (1/rho) dP/dr for P = K rho^Gamma (checked away from the floor)
+    st, eos_r, ext, eos, prof = I.relax_state(400, seed=2)
+    K, G = float(eos_r["K"][0]), float(eos_r["Gamma"][0])
+    nr = ext["nr"]
+    grid = np.linspace(0.0, ext["r_max"][0], nr)
+    rho_t = np.interp(grid, prof.rbar, prof.rho * prof.psi4 ** 1.5)
+    P = K * rho_t ** G
+    dPdr = np.gradient(P, grid, edge_order=2)
+    inner = (grid > 0.05 * grid[-1]) & (grid < 0.9 * grid[-1])
+    want = dPdr[inner] / rho_t[inner]
+    got = ext["g"][0][inner]
+    assert np.all(got < 0.0)  # inward
+    assert np.max(np.abs(got - want) / np.abs(want)) < 1e-3
+
+
+def test_oracle_relaxation_settles():
+    # damped relaxation of a jittered star in its external field: the kinetic
+    # energy it picks up decays and the residual force drops
+    st, eos_r, ext, eos, prof = I.relax_state(1200, seed=3)
+    mat = dict(I.DEFAULT_MATERIAL)
+    dt = I.cfl_dt(st, eos_r)
+    r0 = oracle.rhs(st, eos_r, mat, None, external=ext)
+    a0 = np.sqrt(np.mean(r0["ax"] ** 2 + r0["ay"] ** 2 + r0["az"] ** 2))
+    ke = []
+    s, rates = st, None
+    for _ in range(6):
+        s, rates = oracle.step(s, eos_r, mat, None, dt, 10, rates=rates, external=ext)
+        ke.append(0.5 * np.sum(s["m"] * (s["vx"] ** 2 + s["vy"] ** 2 + s["vz"] ** 2)))
+    a1 = np.sqrt(np.mean(rates["ax"] ** 2 + rates["ay"] ** 2 + rates["az"] ** 2))
+    assert ke[-1] < 0.5 * max(ke), ke
+    assert a1 < 0.5 * a0, (a0, a1)
