@@ -262,9 +262,17 @@ def run_ours(args):
         st, eos, met = select_stars(full, eos_all, met_all, mine)
         dt = 0.5 * I.cfl_dt(st, eos)
         nst = len(mine)
+    elif args.workload == "relax":
+        # relaxation of a jittered star in its external potential (Sec. II.A):
+        # relaxation EoS (Gamma = 1.01), g_eff table, wall, damping; no metric
+        st, eos, ext, _, _ = I.relax_state(args.n, seed=1 + rank)
+        met = None
+        dt = I.cfl_dt(st, eos)
+        nst = 1
     else:
         st, eos, met, dt = make_star(1 + rank, args.n)
         nst = 1
+    external = ext if args.workload == "relax" else None
     n = len(st["x"])
     prec = sph.SPH_MIXED if args.precision == "mixed" else sph.SPH_FP64
     stream = torch.cuda.Stream()
@@ -273,6 +281,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     ctx = sph.sph_init(dstate, eos, I.DEFAULT_MATERIAL, met, prec,
                        dict(h_nmin=55, h_nmax=65, use_graph=1), stream=stream.cuda_stream)
+    if external is not None:
+        sph.sph_set_external(ctx, external)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sph.sph_timing(ctx, True)
     with torch.cuda.stream(stream):
@@ -364,6 +374,9 @@ def run_ours(args):
             "workload": ("TOV star, %d particles (M=1.4, R=12 km, Gamma=2, 5%% crust), "
                          "isotropic background, one KDK step per timed step incl. sort and "
                          "neighbour lists" % n) if args.workload == "star" else
+                        ("relaxation of a jittered %d-particle star in its external potential "
+                         "(Gamma 1.01, g_eff table, wall, damping), one KDK step per timed step"
+                         % n) if args.workload == "relax" else
                         ("ensemble of %d stars (log-uniform N, Gamma 1.8-2.5, crust 3-10%%), "
                          "%d particles on this GPU, one launch per kernel for all stars"
                          % (args.nstars, n)),
@@ -391,6 +404,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         c64 = sph.sph_init(d64, eos, I.DEFAULT_MATERIAL, met, sph.SPH_FP64,
                            dict(h_nmin=55, h_nmax=65, use_graph=1), stream=stream.cuda_stream)
+        if external is not None:
+            sph.sph_set_external(c64, external)
         t64, p64 = time_steps(c64, dt, args.fp64_steps, 3, flush, stream)
         sph.sph_free(c64)
         del d64
@@ -656,7 +671,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--n", type=int, default=N_STAR)
-    ap.add_argument("--workload", choices=("star", "ensemble"), default="star")
+    ap.add_argument("--workload", choices=("star", "ensemble", "relax"), default="star")
     ap.add_argument("--nstars", type=int, default=64)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--cpu-sample", type=int, default=0,

@@ -411,8 +411,10 @@ __device__ __forceinline__ void finalize(int64_t i, int c, int64_t N, const DevS
 enum { A_P0, A_P1, A_P2, A_X0, A_X1, A_X2, A_DU, A_DUC, A_DD, A_G00, A_G01, A_G02, A_G10, A_G11,
        A_G12, A_G20, A_G21, A_G22, A_N };
 
+// (6 blocks of 128 threads per SM: at most 85 registers, which keeps the
+// register allocation at 80 per thread)
 template <int LPI, int R>
-__global__ void __launch_bounds__(kTB)
+__global__ void __launch_bounds__(kTB, 6)
 k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
               DevRates out, int cap)
 {
