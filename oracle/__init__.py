@@ -49,7 +49,8 @@ class _State(C.Structure):
 
 
 class _Eos(C.Structure):
-    _fields_ = [("nstars", C.c_int32), ("K", _d), ("Gamma", _d)]
+    _fields_ = [("nstars", C.c_int32), ("K", _d), ("Gamma", _d), ("npieces", C.c_int32),
+                ("rho_bound", _d), ("Gamma_above", _d)]
 
 
 class _Material(C.Structure):
@@ -116,6 +117,8 @@ def lib():
                                        _d, _d, _d, _d]
             L.ora_external_accel.argtypes = [C.POINTER(_External), C.c_int, C.c_double,
                                              C.c_double, C.c_double, _d, _d, _d]
+            L.ora_eos_eval_star.argtypes = [C.POINTER(_Eos), C.c_int, C.c_double, C.c_int,
+                                            _d, _d, _d, _d]
             L.ora_num_threads.restype = C.c_int
             L.ora_set_threads.argtypes = [C.c_int]
             _lib = L
@@ -149,10 +152,17 @@ def _cstate(s: dict) -> _State:
 
 
 def _ceos(eos: dict, keep: list) -> _Eos:
+    """ctypes view of an EoS dict: K, Gamma per star; optional piecewise
+    rho_bound and Gamma_above of shape (nstars, npieces - 1)."""
     K = np.ascontiguousarray(eos["K"], dtype=np.float64).ravel()
     G = np.ascontiguousarray(eos["Gamma"], dtype=np.float64).ravel()
     keep += [K, G]
-    return _Eos(len(K), _p(K), _p(G))
+    if eos.get("rho_bound") is None:
+        return _Eos(len(K), _p(K), _p(G), 0, None, None)
+    rb = np.ascontiguousarray(eos["rho_bound"], dtype=np.float64).reshape(len(K), -1)
+    ga = np.ascontiguousarray(eos["Gamma_above"], dtype=np.float64).reshape(len(K), -1)
+    keep += [rb, ga]
+    return _Eos(len(K), _p(K), _p(G), rb.shape[1] + 1, _p(rb), _p(ga))
 
 
 def _cmat(mat: dict) -> _Material:
@@ -363,6 +373,16 @@ def eos_eval(K: float, Gamma: float, rho: float, relativistic: bool):
     o = [np.zeros(1) for _ in range(4)]
     lib().ora_eos_eval(float(K), float(Gamma), float(rho), int(relativistic), *[_p(a) for a in o])
     return tuple(float(a[0]) for a in o)  # P, u, dP/drho, c_s
+
+
+def eos_eval_star(eos: dict, star: int, rho: float, relativistic: bool):
+    """(P, u, dP/drho, c_s) of star `star` at rho, with any number of pieces."""
+    keep: list = []
+    ce = _ceos(eos, keep)
+    o = [np.zeros(1) for _ in range(4)]
+    lib().ora_eos_eval_star(C.byref(ce), int(star), float(rho), int(relativistic),
+                            *[_p(a) for a in o])
+    return tuple(float(a[0]) for a in o)
 
 
 def metric_eval(metric: dict, star: int, x: float, y: float, z: float):

@@ -49,7 +49,15 @@ typedef struct {
 
 typedef struct {
     int32_t nstars;
-    const double *K, *Gamma; /* per star, P = K rho^Gamma (Eq. poly_eos) */
+    const double *K, *Gamma; /* per star, P = K rho^Gamma (Eq. poly_eos); with pieces: piece 0 */
+    /* Piecewise polytrope (Sec. II.A, "several polytropic models ... connected",
+     * after Read et al. 2009): npieces 0 or 1 is the single polytrope.  With
+     * npieces = p > 1, piece k+1 starts at rho_bound[s*(p-1)+k] (ascending)
+     * with exponent Gamma_above[s*(p-1)+k]; its K follows from continuity of
+     * P and the constant a of u = a + K rho^(Gamma-1)/(Gamma-1) from
+     * continuity of u. */
+    int32_t npieces;
+    const double *rho_bound, *Gamma_above;
 } ora_eos;
 
 typedef struct {
@@ -292,6 +300,39 @@ static double gen_lorentz(double alpha, double psi4, const double *xdot)
 /* Newtonian c_s = sqrt(dP/drho), relativistic c_s = sqrt(dP/drho /          */
 /* (1 + u + P/rho)), bulk modulus B = Gamma P (Eq. bulk_modulus).            */
 /* ------------------------------------------------------------------------ */
+/* The piece of star st's EoS that holds density rho: its K, Gamma and the
+ * energy constant a (u = a + K rho^(Gamma-1)/(Gamma-1)). */
+void ora_eos_piece(const ora_eos *e, int st, double rho, double *K, double *G, double *a)
+{
+    double Ki = e->K[st], Gi = e->Gamma[st], ai = 0.0;
+    int np = e->npieces > 1 ? e->npieces : 1;
+    for (int k = 0; k + 1 < np; ++k) {
+        double rb = e->rho_bound[(int64_t)st * (np - 1) + k];
+        if (!(rho >= rb)) break;
+        double Gn = e->Gamma_above[(int64_t)st * (np - 1) + k];
+        double Kn = Ki * pow(rb, Gi - Gn);                        /* P continuous at rb */
+        ai += Ki * pow(rb, Gi - 1.0) / (Gi - 1.0) - Kn * pow(rb, Gn - 1.0) / (Gn - 1.0);
+        Ki = Kn;
+        Gi = Gn;
+    }
+    *K = Ki;
+    *G = Gi;
+    *a = ai;
+}
+
+/* P, u, dP/drho and c_s of star st at density rho (any number of pieces). */
+void ora_eos_eval_star(const ora_eos *e, int st, double rho, int relativistic, double *P,
+                       double *u, double *cP, double *cs)
+{
+    double K, G, a;
+    ora_eos_piece(e, st, rho, &K, &G, &a);
+    *P = K * pow(rho, G);
+    *u = a + K * pow(rho, G - 1.0) / (G - 1.0);
+    *cP = G * K * pow(rho, G - 1.0);
+    if (relativistic) *cs = sqrt(*cP / (1.0 + *u + *P / rho));
+    else *cs = sqrt(*cP);
+}
+
 void ora_eos_eval(double K, double Gamma, double rho, int relativistic,
                   double *P, double *u, double *cP, double *cs)
 {
@@ -364,7 +405,7 @@ static void prep_particle(const ora_state *s, const double *vx, const double *vy
         for (int k = 0; k < 3; ++k) { p->grad_alpha[k] = 0.0; p->grad_psi4[k] = 0.0; }
         p->rho = D;
     }
-    ora_eos_eval(eos->K[st], eos->Gamma[st], p->rho, g && g->kind == 1,
+    ora_eos_eval_star(eos, st, p->rho, g && g->kind == 1,
                  &p->P, &p->ue, &p->cP, &p->cs);
     p->henth = 1.0 + p->ue + p->P / p->rho;
     p->PD2 = p->P / (D * D);
@@ -831,7 +872,9 @@ int ora_step(ora_state *s, const ora_eos *eos, const ora_material *mat, const or
                 }
                 get_S(s, s->S, a, s6);
                 int st = star_of(s, a);
-                if (ora_breaks(s6, r->P[a], eos->Gamma[st], s->mu[a], s->eps_break[a],
+                double Kp, Gp, ap;  /* B = rho dP/drho = Gamma_piece P */
+                ora_eos_piece(eos, st, r->rho[a], &Kp, &Gp, &ap);
+                if (ora_breaks(s6, r->P[a], Gp, s->mu[a], s->eps_break[a],
                                mat->break_stress)) {
                     s->flags[a] |= 2u;
                     if (mat->break_zero_S) {

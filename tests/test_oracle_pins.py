@@ -539,3 +539,46 @@ def test_oracle_relaxation_settles():
     a1 = np.sqrt(np.mean(rates["ax"] ** 2 + rates["ay"] ** 2 + rates["az"] ** 2))
     assert ke[-1] < 0.5 * max(ke), ke
     assert a1 < 0.5 * a0, (a0, a1)
+
+
+# ------------------------------------------------------ piecewise polytrope
+# Several polytropes joined at dividing densities (Sec. II.A, after Read et
+# al. 2009): P and u continuous, first law u' = P/rho^2 piece by piece.
+_PP = dict(K=[0.05], Gamma=[1.35], rho_bound=[[2e-4, 8e-4]], Gamma_above=[[3.0, 2.6]])
+
+
+def test_piecewise_eos_continuous_at_bounds():
+    gam = [_PP["Gamma"][0]] + list(_PP["Gamma_above"][0])
+    for k, rb in enumerate(_PP["rho_bound"][0]):
+        lo = oracle.eos_eval_star(_PP, 0, rb * (1 - 1e-12), False)
+        hi = oracle.eos_eval_star(_PP, 0, rb * (1 + 1e-12), False)
+        assert abs(hi[0] - lo[0]) <= 1e-10 * lo[0]  # P
+        assert abs(hi[1] - lo[1]) <= 1e-10 * lo[1]  # u
+        # dP/drho = Gamma P/rho with P continuous: it jumps by Gamma_above/Gamma_below
+        assert abs(hi[2] / lo[2] - gam[k + 1] / gam[k]) < 1e-9
+
+
+def test_piecewise_eos_first_law():
+    # u(rho2) - u(rho1) = int P/rho^2 drho across both dividing densities
+    from scipy.integrate import quad
+
+    r1, r2 = 5e-5, 3e-3
+    P = lambda r: oracle.eos_eval_star(_PP, 0, r, False)[0]
+    pts = list(_PP["rho_bound"][0])
+    du, _ = quad(lambda r: P(r) / r ** 2, r1, r2, points=pts, epsabs=0, epsrel=1e-12, limit=200)
+    u1 = oracle.eos_eval_star(_PP, 0, r1, False)[1]
+    u2 = oracle.eos_eval_star(_PP, 0, r2, False)[1]
+    assert abs((u2 - u1) - du) <= 1e-9 * abs(du)
+    # dP/drho is the derivative of P inside each piece
+    for r in (1e-4, 5e-4, 2e-3):
+        h = 1e-6 * r
+        d = (P(r + h) - P(r - h)) / (2 * h)
+        assert abs(oracle.eos_eval_star(_PP, 0, r, False)[2] / d - 1.0) < 1e-7
+
+
+def test_piecewise_with_one_piece_is_the_polytrope():
+    one = dict(K=[0.05], Gamma=[1.35])
+    for r in (1e-5, 1e-3, 0.1):
+        a = oracle.eos_eval_star(one, 0, r, True)
+        b = oracle.eos_eval(0.05, 1.35, r, True)
+        assert a == b
