@@ -68,10 +68,20 @@ typedef struct {
     double *mu, *Y0, *eps_break;
 } sph_particles;
 
-/* Polytropic equation of state per star, P = K rho^Gamma (Eq. poly_eos). */
+/* Polytropic equation of state per star, P = K rho^Gamma (Eq. poly_eos), or a
+ * piecewise polytrope ("several polytropic models ... connected", Sec. II.A,
+ * after Read et al. 2009).  npieces 0 or 1: one polytrope (the other piece
+ * fields are ignored and may be NULL).  npieces = p in 2..8: K[s], Gamma[s]
+ * give piece 0; piece k+1 starts at rho_bound[s*(p-1)+k] (positive,
+ * increasing) with exponent Gamma_above[s*(p-1)+k] > 1; its K follows from
+ * continuity of P and u = a + K rho^(Gamma-1)/(Gamma-1) from continuity of u.
+ * All host arrays; fields after Gamma may be zero-initialised by callers that
+ * use one polytrope. */
 typedef struct {
     int32_t nstars;
     const double *K, *Gamma; /* host arrays of nstars */
+    int32_t npieces;
+    const double *rho_bound, *Gamma_above;
 } sph_eos;
 
 /* Material and scheme options (host).  alpha_av, beta_av, eta2: Monaghan

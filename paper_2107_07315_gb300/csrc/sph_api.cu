@@ -56,6 +56,8 @@ struct sph_ctx {
     // owned device memory
     std::vector<void *> allocs;
     double *d_K = nullptr, *d_Gamma = nullptr;
+    int npieces = 0;                                   // piecewise EoS (0: one polytrope)
+    double *d_rho_b = nullptr, *d_Kp = nullptr, *d_Gp = nullptr, *d_ap = nullptr;
     DevMaterial mat{};
     DevMetric met{};
     Scratch s{};
@@ -157,7 +159,93 @@ DevEos eos_of(const sph_ctx *c)
     DevEos e;
     e.K = c->d_K;
     e.Gamma = c->d_Gamma;
+    e.npieces = c->npieces;
+    e.rho_b = c->d_rho_b;
+    e.Kp = c->d_Kp;
+    e.Gp = c->d_Gp;
+    e.ap = c->d_ap;
     return e;
+}
+
+constexpr int kMaxPieces = 8;
+
+// Checks an EoS for nstars stars (one polytrope or a piecewise one).
+sph_status check_eos(const sph_eos *eos, int nstars_expected)
+{
+    if (!eos || eos->nstars < 1 || eos->nstars > 65535 || !eos->K || !eos->Gamma)
+        return fail(SPH_ERR_ARG, "eos must give 1..65535 stars with K and Gamma");
+    if (nstars_expected > 0 && eos->nstars != nstars_expected)
+        return fail(SPH_ERR_ARG, "eos must give K and Gamma for each of the %d stars",
+                    nstars_expected);
+    for (int s = 0; s < eos->nstars; ++s) {
+        if (!(eos->Gamma[s] > 1.0) || !(eos->K[s] > 0.0) || !std::isfinite(eos->Gamma[s]) ||
+            !std::isfinite(eos->K[s]))
+            return fail(SPH_ERR_ARG, "star %d: need K > 0 and Gamma > 1", s);
+    }
+    const int np = eos->npieces;
+    if (np < 0 || np > kMaxPieces) return fail(SPH_ERR_ARG, "npieces must be 0..%d", kMaxPieces);
+    if (np > 1) {
+        if (!eos->rho_bound || !eos->Gamma_above)
+            return fail(SPH_ERR_ARG, "piecewise eos needs rho_bound and Gamma_above");
+        for (int s = 0; s < eos->nstars; ++s)
+            for (int k = 0; k + 1 < np; ++k) {
+                const double rb = eos->rho_bound[(size_t)s * (np - 1) + k];
+                const double ga = eos->Gamma_above[(size_t)s * (np - 1) + k];
+                if (!(rb > 0.0) || !std::isfinite(rb) || !(ga > 1.0) || !std::isfinite(ga))
+                    return fail(SPH_ERR_ARG, "star %d piece %d: need rho_bound > 0, Gamma > 1", s,
+                                k + 1);
+                if (k > 0 && !(rb > eos->rho_bound[(size_t)s * (np - 1) + k - 1]))
+                    return fail(SPH_ERR_ARG, "star %d: rho_bound must increase", s);
+            }
+    }
+    return SPH_OK;
+}
+
+// Copies a checked EoS into the context; for a piecewise one, K and the
+// energy constant of each piece follow from continuity of P and u at the
+// dividing densities.
+sph_status upload_eos(sph_ctx *c, const sph_eos *eos)
+{
+    const int ns = eos->nstars;
+    if (!c->d_K) {
+        STATUS_TRY(c->alloc(&c->d_K, ns));
+        STATUS_TRY(c->alloc(&c->d_Gamma, ns));
+    }
+    CUDA_TRY(cudaMemcpy(c->d_K, eos->K, ns * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_Gamma, eos->Gamma, ns * sizeof(double), cudaMemcpyHostToDevice));
+    c->npieces = eos->npieces > 1 ? eos->npieces : 0;
+    if (c->npieces > 1) {
+        const int np = c->npieces;
+        std::vector<double> rb((size_t)ns * (np - 1)), Kp((size_t)ns * np), Gp(Kp.size()),
+            ap(Kp.size());
+        for (int s = 0; s < ns; ++s) {
+            double K = eos->K[s], G = eos->Gamma[s], a = 0.0;
+            Kp[(size_t)s * np] = K;
+            Gp[(size_t)s * np] = G;
+            ap[(size_t)s * np] = 0.0;
+            for (int k = 0; k + 1 < np; ++k) {
+                const double r = eos->rho_bound[(size_t)s * (np - 1) + k];
+                const double Gn = eos->Gamma_above[(size_t)s * (np - 1) + k];
+                const double Kn = K * std::pow(r, G - Gn);
+                a += K * std::pow(r, G - 1.0) / (G - 1.0) - Kn * std::pow(r, Gn - 1.0) / (Gn - 1.0);
+                K = Kn;
+                G = Gn;
+                rb[(size_t)s * (np - 1) + k] = r;
+                Kp[(size_t)s * np + k + 1] = K;
+                Gp[(size_t)s * np + k + 1] = G;
+                ap[(size_t)s * np + k + 1] = a;
+            }
+        }
+        STATUS_TRY(c->alloc(&c->d_rho_b, rb.size()));
+        STATUS_TRY(c->alloc(&c->d_Kp, Kp.size()));
+        STATUS_TRY(c->alloc(&c->d_Gp, Gp.size()));
+        STATUS_TRY(c->alloc(&c->d_ap, ap.size()));
+        CUDA_TRY(cudaMemcpy(c->d_rho_b, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->d_Kp, Kp.data(), Kp.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->d_Gp, Gp.data(), Gp.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->d_ap, ap.data(), ap.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return SPH_OK;
 }
 
 DevRates rates_of(const sph_rates *o)
@@ -347,13 +435,7 @@ sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_materi
             !p->S || !p->type || !p->flags)
             return fail(SPH_ERR_ARG, "a required particle array is NULL");
     }
-    if (!eos || eos->nstars < 1 || eos->nstars > 65535 || !eos->K || !eos->Gamma)
-        return fail(SPH_ERR_ARG, "eos must give 1..65535 stars with K and Gamma");
-    for (int s = 0; s < eos->nstars; ++s) {
-        if (!(eos->Gamma[s] > 1.0) || !(eos->K[s] > 0.0) || !std::isfinite(eos->Gamma[s]) ||
-            !std::isfinite(eos->K[s]))
-            return fail(SPH_ERR_ARG, "star %d: need K > 0 and Gamma > 1", s);
-    }
+    STATUS_TRY(check_eos(eos, 0));
     if (!mat) return fail(SPH_ERR_ARG, "material is NULL");
     if (mat->jaumann < 0 || mat->jaumann > 1 || mat->yield_mode < 0 || mat->yield_mode > 1 ||
         mat->break_stress < 0 || mat->break_stress > 1)
@@ -504,10 +586,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     STATUS_TRY(c->alloc(&c->zeros, nn));
     CUDA_TRY(cudaMemset(c->zeros, 0, nn * sizeof(double)));
     // EoS, material, metric.
-    STATUS_TRY(c->alloc(&c->d_K, c->nstars));
-    STATUS_TRY(c->alloc(&c->d_Gamma, c->nstars));
-    CUDA_TRY(cudaMemcpy(c->d_K, eos->K, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->d_Gamma, eos->Gamma, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
+    STATUS_TRY(upload_eos(c, eos));
     c->mat.alpha_av = mat->alpha_av;
     c->mat.beta_av = mat->beta_av;
     c->mat.eta2 = mat->eta2;
@@ -757,16 +836,9 @@ sph_status sph_set_external(sph_ctx *c, const sph_external *e)
 sph_status sph_relax_finish(sph_ctx *c, const sph_eos *eos)
 {
     if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
-    if (!eos || eos->nstars != c->nstars || !eos->K || !eos->Gamma)
-        return fail(SPH_ERR_ARG, "eos must give K and Gamma for each of the %d stars", c->nstars);
-    for (int s = 0; s < eos->nstars; ++s) {
-        if (!(eos->Gamma[s] > 1.0) || !(eos->K[s] > 0.0) || !std::isfinite(eos->Gamma[s]) ||
-            !std::isfinite(eos->K[s]))
-            return fail(SPH_ERR_ARG, "star %d: need K > 0 and Gamma > 1", s);
-    }
+    STATUS_TRY(check_eos(eos, c->nstars));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    CUDA_TRY(cudaMemcpy(c->d_K, eos->K, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->d_Gamma, eos->Gamma, c->nstars * sizeof(double), cudaMemcpyHostToDevice));
+    STATUS_TRY(upload_eos(c, eos));
     c->met.ext_kind = 0;
     drop_graph(c);
     if (c->n > 0) {

@@ -78,9 +78,34 @@ struct DevState {
     const int32_t *star;             // may be null
 };
 
+// Equation of state per star: P = K rho^Gamma (Eq. poly_eos), or a piecewise
+// polytrope (npieces > 1): piece k of star s holds rho >= rho_b[s*(np-1)+k-1]
+// with Kp, Gp and the energy constant ap (u = a + K rho^(Gamma-1)/(Gamma-1))
+// at [s*np + k], K and a fixed by continuity of P and u.
 struct DevEos {
     const double *K, *Gamma;
+    int npieces;
+    const double *rho_b, *Kp, *Gp, *ap;
 };
+
+// The piece of star s's EoS that holds density rho: K, Gamma and a.
+template <typename T>
+__device__ __forceinline__ void eos_piece(const DevEos &e, int s, T rho, T &K, T &G, T &a)
+{
+    if (e.npieces <= 1) {
+        K = (T)e.K[s];
+        G = (T)e.Gamma[s];
+        a = (T)0;
+        return;
+    }
+    int k = 0;
+    for (int j = 0; j + 1 < e.npieces; ++j)
+        if (rho >= (T)e.rho_b[s * (e.npieces - 1) + j]) k = j + 1;
+    const int o = s * e.npieces + k;
+    K = (T)e.Kp[o];
+    G = (T)e.Gp[o];
+    a = (T)e.ap[o];
+}
 
 struct DevMaterial {
     double alpha_av, beta_av, eta2;

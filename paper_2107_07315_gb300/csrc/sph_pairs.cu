@@ -98,7 +98,6 @@ __device__ __forceinline__ Prep<T> eos_prep(const DevEos &eos, const DevMetric &
                                             T D, T vx, T vy, T vz, double x, double y, double z)
 {
     Prep<T> p;
-    T K = (T)eos.K[star], G = (T)eos.Gamma[star];
     bool metric = g.kind == 1;
     if (metric) {
         T al, ga[3], q4, gq[3];
@@ -113,9 +112,11 @@ __device__ __forceinline__ Prep<T> eos_prep(const DevEos &eos, const DevMetric &
         p.rho = D;
         p.Wt = (T)1;
     }
+    T K, G, ea;
+    eos_piece<T>(eos, star, p.rho, K, G, ea);
     T rg1 = pow(p.rho, G - (T)1);
     p.P = K * p.rho * rg1;
-    T ue = K * rg1 / (G - (T)1);
+    T ue = ea + K * rg1 / (G - (T)1);
     p.cP = G * K * rg1;
     p.henth = (T)1 + ue + p.P / p.rho;
     p.cs = metric ? sqrt(p.cP / p.henth) : sqrt(p.cP);

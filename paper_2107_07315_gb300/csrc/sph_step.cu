@@ -12,15 +12,16 @@ namespace sph {
 namespace {
 
 // Modification step after a relaxation (Sec. II.A): the specific internal
-// energy of the polytrope, u = K rho^(Gamma-1)/(Gamma-1), for the density of
-// the last right-hand side.
+// energy of the (piecewise) polytrope, u = a + K rho^(Gamma-1)/(Gamma-1), for
+// the density of the last right-hand side.
 __global__ void k_set_u(StepState s, DevRates r, DevEos eos)
 {
     int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a >= s.n) return;
     const int star = s.star ? s.star[a] : 0;
-    const double K = eos.K[star], G = eos.Gamma[star];
-    s.u[a] = K * pow(r.rho[a], G - 1.0) / (G - 1.0);
+    double K, G, ea;
+    eos_piece<double>(eos, star, r.rho[a], K, G, ea);
+    s.u[a] = ea + K * pow(r.rho[a], G - 1.0) / (G - 1.0);
 }
 
 // Half kick, drift, and the predicted velocity/stress used by the RHS.
@@ -123,7 +124,9 @@ __global__ void k_kick_return(StepState s, DevRates r, DevEos eos, DevMaterial m
         // maximum-strain test: eps = sigma_max/E, E = 9 B mu/(3B + mu), B = Gamma P
         int star = s.star ? s.star[a] : 0;
         double P = r.P[a];
-        double B = eos.Gamma[star] * P;
+        double Kp, Gp, ap;  // B = rho dP/drho = Gamma P of the piece holding rho
+        eos_piece<double>(eos, star, r.rho[a], Kp, Gp, ap);
+        double B = Gp * P;
         double mu = s.mu[a];
         double E = 9.0 * B * mu / (3.0 * B + mu);
         if (E > 0.0) {

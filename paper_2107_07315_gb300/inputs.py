@@ -63,6 +63,7 @@ class TovProfile:
     dalpha: np.ndarray   # d alpha / d rbar
     psi4: np.ndarray
     dpsi4: np.ndarray    # d psi^4 / d rbar
+    eos: dict | None = None  # the star's EoS (piecewise polytropes); K, Gamma: central piece
 
 
 def _eos(K, Gamma, P):
@@ -157,6 +158,111 @@ def tov_solve(K: float, Gamma: float, rho_c: float, npts: int = 4000) -> TovProf
     Mb = float(np.trapezoid(integrand, rbar))
     return TovProfile(K, Gamma, rho_c, M, Rs, rbar_s, Mb, rbar, rho, P, u, alpha, dalpha,
                       psi4, dpsi4)
+
+
+def eos_pieces(eos: dict, star: int = 0):
+    """(rho_b, K, Gamma, a) per piece of a (piecewise) polytrope: piece k holds
+    rho >= rho_b[k-1]; K and a (u = a + K rho^(Gamma-1)/(Gamma-1)) follow from
+    continuity of P and u at the dividing densities."""
+    K = [float(np.ravel(eos["K"])[star])]
+    G = [float(np.ravel(eos["Gamma"])[star])]
+    a = [0.0]
+    rb = []
+    if eos.get("rho_bound") is not None:
+        nb = np.asarray(eos["rho_bound"], np.float64).reshape(len(np.ravel(eos["K"])), -1)[star]
+        ga = np.asarray(eos["Gamma_above"], np.float64).reshape(len(np.ravel(eos["K"])), -1)[star]
+        for r, gn in zip(nb, ga):
+            kn = K[-1] * r ** (G[-1] - gn)
+            a.append(a[-1] + K[-1] * r ** (G[-1] - 1.0) / (G[-1] - 1.0)
+                     - kn * r ** (gn - 1.0) / (gn - 1.0))
+            K.append(kn)
+            G.append(float(gn))
+            rb.append(float(r))
+    return np.array(rb), np.array(K), np.array(G), np.array(a)
+
+
+def eos_eval_pieces(eos: dict, rho, star: int = 0):
+    """P, u and dP/drho of a (piecewise) polytrope at densities rho (arrays)."""
+    rb, K, G, a = eos_pieces(eos, star)
+    rho = np.asarray(rho, np.float64)
+    k = np.searchsorted(rb, rho, side="right")
+    Kk, Gk, ak = K[k], G[k], a[k]
+    r = np.maximum(rho, 0.0)
+    P = Kk * r ** Gk
+    u = ak + Kk * r ** (Gk - 1.0) / (Gk - 1.0)
+    return P, u, Gk * Kk * r ** (Gk - 1.0)
+
+
+def tov_solve_pieces(eos: dict, rho_c: float, npts: int = 4000) -> TovProfile:
+    """TOV structure for a (piecewise) polytrope, integrated in the areal
+    radius R with the pressure as variable:
+      dP/dR = -(e + P)(m + 4 pi R^3 P)/(R (R - 2m)),  dm/dR = 4 pi R^2 e,
+      e = rho (1 + u), with the lapse and isotropic radius as in tov_solve;
+    ends where P falls to 1e-14 of the central pressure."""
+    from scipy.integrate import solve_ivp
+
+    rb, Kp, Gp, ap = eos_pieces(eos)
+    Pb = Kp[1:] * rb ** Gp[1:] if len(rb) else np.array([])
+
+    def rho_of_P(P):
+        P = max(P, 0.0)
+        k = int(np.searchsorted(Pb, P, side="right"))
+        return (P / Kp[k]) ** (1.0 / Gp[k]), k
+
+    Pc, uc, _ = (float(v) for v in eos_eval_pieces(eos, rho_c))
+    ec = rho_c * (1.0 + uc)
+
+    def f(R, y):
+        P, m, _phi, _w = y
+        rho, k = rho_of_P(P)
+        u = ap[k] + Kp[k] * rho ** (Gp[k] - 1.0) / (Gp[k] - 1.0) if rho > 0 else 0.0
+        e = rho * (1.0 + u)
+        g = (m + 4.0 * math.pi * R ** 3 * P) / (R * (R - 2.0 * m))
+        return [-(e + P) * g, 4.0 * math.pi * R * R * e, g,
+                (1.0 / math.sqrt(1.0 - 2.0 * m / R) - 1.0) / R]
+
+    L = 1.0 / math.sqrt(ec)
+    R0 = 1e-6 * L
+    y0 = [Pc - (2.0 * math.pi / 3.0) * (ec + Pc) * (ec + 3.0 * Pc) * R0 * R0,
+          4.0 / 3.0 * math.pi * ec * R0 ** 3, 0.0, 0.0]
+    surf = lambda R, y: y[0] - 1e-14 * Pc
+    surf.terminal, surf.direction = True, -1
+    sol = solve_ivp(f, (R0, 100.0 * L), y0, method="DOP853", rtol=1e-11,
+                    atol=[1e-16 * Pc, 1e-18 * L, 1e-15, 1e-15], events=surf, dense_output=True)
+    if not sol.success or not len(sol.t_events[0]):
+        raise RuntimeError("TOV integration (pieces) failed: " + sol.message)
+    Rs = float(sol.t_events[0][0])
+    ys = sol.sol(Rs)
+    M = float(ys[1])
+    R = np.linspace(0.0, Rs, npts)
+    Y = sol.sol(np.maximum(R, R0))
+    P = np.where(R > R0, np.maximum(Y[0], 0.0), Pc)
+    m = np.where(R > R0, Y[1], 4.0 / 3.0 * math.pi * ec * R ** 3)
+    rho = np.array([rho_of_P(x)[0] for x in P])
+    _, u, _ = eos_eval_pieces(eos, rho)
+    phi = np.where(R > R0, Y[2], 0.0) + 0.5 * math.log(1.0 - 2.0 * M / Rs) - float(ys[2])
+    rbar_s = 0.5 * (Rs - M + math.sqrt(Rs * Rs - 2.0 * M * Rs))
+    w = np.where(R > R0, Y[3], 0.0) + math.log(rbar_s / Rs) - float(ys[3])
+    kc = int(np.searchsorted(rb, rho_c, side="right"))
+    return _isotropic_profile(float(Kp[kc]), float(Gp[kc]), rho_c, M, Rs, rbar_s, R, m, rho, P,
+                              u, phi, w, eos)
+
+
+def _isotropic_profile(K, Gamma, rho_c, M, Rs, rbar_s, R, m, rho, P, u, phi, w, eos=None):
+    """TovProfile on the isotropic radius from areal-radius arrays: rbar = R e^w,
+    alpha = e^phi, psi^4 = (R/rbar)^2 and their rbar-derivatives."""
+    rbar = R * np.exp(w)
+    alpha = np.exp(phi)
+    Rs_ = np.where(R > 0, R, 1.0)
+    g = np.where(R > 0, (m + 4.0 * math.pi * R ** 3 * P) / (Rs_ * (Rs_ - 2.0 * m)), 0.0)
+    dRdrb = np.sqrt(np.maximum(1.0 - 2.0 * m / Rs_, 0.0)) / np.exp(w)
+    psi4 = np.exp(-2.0 * w)
+    rb_ = np.where(rbar > 0, rbar, 1.0)
+    dpsi4 = np.where(rbar > 0, 2.0 * (R / rb_) * (dRdrb - R / rb_) / rb_, 0.0)
+    dalpha = alpha * g * dRdrb
+    Mb = float(np.trapezoid(rho * psi4 ** 1.5 * 4.0 * math.pi * rbar ** 2, rbar))
+    return TovProfile(K, Gamma, rho_c, M, Rs, rbar_s, Mb, rbar, rho, P, u, alpha, dalpha, psi4,
+                      dpsi4, eos)
 
 
 def solve_star(Gamma: float, M_target: float = 1.4, R_target_km: float = 12.0):
@@ -339,7 +445,11 @@ def star_state(N: int, Gamma: float = 2.0, seed: int = 1, crust_frac: float = 0.
     P = np.interp(r, prof.rbar, prof.P)
     u = np.interp(r, prof.rbar, prof.u)
     st["u"][:] = u
-    cs = np.sqrt(np.maximum(prof.Gamma * prof.K * rho ** (prof.Gamma - 1.0), 0.0)
+    if prof.eos is not None:
+        dPdrho = eos_eval_pieces(prof.eos, rho)[2]
+    else:
+        dPdrho = prof.Gamma * prof.K * rho ** (prof.Gamma - 1.0)
+    cs = np.sqrt(np.maximum(dPdrho, 0.0)
                  / (1.0 + u + np.where(rho > 0, P / np.where(rho > 0, rho, 1.0), 0.0)))
     sinr = np.sin(math.pi * np.minimum(r, Rs) / Rs)
     vr = amp_l0 * cs * sinr
@@ -357,7 +467,10 @@ def star_state(N: int, Gamma: float = 2.0, seed: int = 1, crust_frac: float = 0.
     else:
         st["Y0"][crust] = Y0
     st["eps_break"][crust] = eps_break
-    eos = dict(K=np.array([prof.K]), Gamma=np.array([prof.Gamma]))
+    if prof.eos is not None:
+        eos = {k: np.asarray(v, np.float64) for k, v in prof.eos.items()}
+    else:
+        eos = dict(K=np.array([prof.K]), Gamma=np.array([prof.Gamma]))
     metric = metric_tables([prof], [center], nr=nr)
     return st, eos, metric, prof
 

@@ -49,7 +49,22 @@ class sph_particles(C.Structure):
 
 
 class sph_eos(C.Structure):
-    _fields_ = [("nstars", C.c_int32), ("K", _d), ("Gamma", _d)]
+    _fields_ = [("nstars", C.c_int32), ("K", _d), ("Gamma", _d), ("npieces", C.c_int32),
+                ("rho_bound", _d), ("Gamma_above", _d)]
+
+
+def _eos_struct(eos: dict, keep: list):
+    """sph_eos from a dict (K, Gamma per star; optional piecewise rho_bound and
+    Gamma_above of shape (nstars, npieces - 1))."""
+    K, G = _f64(eos["K"]), _f64(eos["Gamma"])
+    keep += [K, G]
+    if eos.get("rho_bound") is None:
+        return sph_eos(len(K), K.ctypes.data_as(_d), G.ctypes.data_as(_d), 0, None, None)
+    rb = np.ascontiguousarray(np.asarray(eos["rho_bound"], np.float64).reshape(len(K), -1))
+    ga = np.ascontiguousarray(np.asarray(eos["Gamma_above"], np.float64).reshape(len(K), -1))
+    keep += [rb, ga]
+    return sph_eos(len(K), K.ctypes.data_as(_d), G.ctypes.data_as(_d), rb.shape[1] + 1,
+                   rb.ctypes.data_as(_d), ga.ctypes.data_as(_d))
 
 
 class sph_material(C.Structure):
@@ -251,13 +266,12 @@ def sph_init(particles: dict, eos: dict, material: dict, metric=None, precision=
     L = lib()
     n = int(particles["x"].numel())
     p = sph_particles(n, *[_ptr(particles.get(k)) for k in PARTICLE_KEYS])
-    K, G = _f64(eos["K"]), _f64(eos["Gamma"])
-    e = sph_eos(len(K), K.ctypes.data_as(_d), G.ctypes.data_as(_d))
+    keep = [particles]
+    e = _eos_struct(eos, keep)
     m = sph_material(float(material.get("alpha_av", 1.0)), float(material.get("beta_av", 2.0)),
                      float(material.get("eta2", 0.01)), int(material.get("jaumann", 0)),
                      int(material.get("yield_mode", 0)), int(material.get("break_stress", 0)),
                      int(material.get("break_zero_S", 0)))
-    keep = [particles, K, G]
     gp = None
     if metric is not None and int(metric.get("kind", 0)) == 1:
         arrs = {k: _f64(metric[k]) for k in ("r_max", "alpha", "dalpha", "psi4", "dpsi4", "M",
@@ -308,8 +322,8 @@ def sph_set_external(ctx: SphCtx, external) -> None:
 
 def sph_relax_finish(ctx: SphCtx, eos: dict) -> None:
     """Modification step after a relaxation: new EoS, u from the density."""
-    K, G = _f64(eos["K"]), _f64(eos["Gamma"])
-    e = sph_eos(len(K), K.ctypes.data_as(_d), G.ctypes.data_as(_d))
+    keep: list = []
+    e = _eos_struct(eos, keep)
     _check(lib().sph_relax_finish(ctx.handle, C.byref(e)), "sph_relax_finish")
 
 

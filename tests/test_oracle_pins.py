@@ -582,3 +582,25 @@ def test_piecewise_with_one_piece_is_the_polytrope():
         a = oracle.eos_eval_star(one, 0, r, True)
         b = oracle.eos_eval(0.05, 1.35, r, True)
         assert a == b
+
+
+def test_tov_pieces_matches_theta_form_and_balances():
+    # one piece: the pressure-form TOV integration reproduces the theta form;
+    # three pieces: the static star is in hydrostatic balance in the oracle's
+    # trajectory equation (pressure coefficient 1/(W~^2 rho h))
+    p1 = I.tov_solve(100.0, 2.0, 0.00128)
+    p2 = I.tov_solve_pieces(dict(K=[100.0], Gamma=[2.0]), 0.00128)
+    assert abs(p1.M / p2.M - 1) < 1e-7 and abs(p1.R / p2.R - 1) < 1e-5
+    pp = dict(K=[100.0], Gamma=[2.0], rho_bound=[[0.0004, 0.001]], Gamma_above=[[2.5, 2.2]])
+    prof = I.tov_solve_pieces(pp, 0.00128)
+    g = I.metric_tables([prof], [(0, 0, 0)], nr=4096)
+    for frac in (0.2, 0.5, 0.8):
+        rb = frac * prof.rbar_s
+        al, ga, q, gq = oracle.metric_eval(g, 0, rb, 0, 0)
+        rho = np.interp(rb, prof.rbar, prof.rho)
+        P, u, _, _ = oracle.eos_eval_star(pp, 0, rho, True)
+        dPdr = np.interp(rb, 0.5 * (prof.rbar[1:] + prof.rbar[:-1]),
+                         np.diff(prof.P) / np.diff(prof.rbar))
+        den = rho * (1 + u + P / rho) / (al * al)
+        acc = oracle.tejeda_accel(al, ga, q, gq, np.zeros(3), np.array([dPdr / den, 0, 0]), 0.0)
+        assert abs(acc[0]) < 2e-3 * abs(al * ga[0] / q), (frac, acc[0])
