@@ -590,6 +590,60 @@ def cube_state(n_side: int = 16, h: float = 1.3, seed: int = 0, K: float = 1.0,
     return st, eos, None, A
 
 
+def lattice_positions(kind: str, n: int, d: float = 1.0) -> np.ndarray:
+    """Points of a simple cubic ("cubic"), face-centred cubic ("fcc") or
+    hexagonal close-packed ("hcp") lattice with nearest-neighbour distance d,
+    n cells (cubic, fcc) or n x n x n sites (hcp) per direction."""
+    if kind == "cubic":
+        g = np.arange(n, dtype=np.float64) * d
+        X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+        return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    if kind == "fcc":
+        a = d * math.sqrt(2.0)                      # cubic cell edge
+        basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) * a
+        g = np.arange(n, dtype=np.float64) * a
+        X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+        cells = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+        return (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    if kind == "hcp":
+        # triangular layers (spacing d), A B A B stacking, layer distance d sqrt(2/3)
+        pts = []
+        for k in range(n):
+            for j in range(n):
+                for i in range(n):
+                    x = d * (i + 0.5 * (j % 2) + (0.5 if k % 2 else 0.0))
+                    y = d * math.sqrt(3.0) / 2.0 * j + (d / (2.0 * math.sqrt(3.0)) if k % 2 else 0.0)
+                    pts.append((x, y, d * math.sqrt(2.0 / 3.0) * k))
+        return np.array(pts, dtype=np.float64)
+    raise ValueError("lattice kind must be cubic, fcc or hcp")
+
+
+def lattice_state(kind: str = "fcc", n: int = 8, d: float = 1.0, h: float = 0.75,
+                  seed: int = 0, K: float = 1.0, Gamma: float = 2.0, vel: float = 0.01,
+                  solid: bool = True):
+    """A block of particles on a lattice (Sec. II.A lists rectangular, hcp and
+    fcc placing): equal masses (density 1 per unit volume of the lattice),
+    smoothing length h, small random velocities, all solid or all fluid."""
+    pos = lattice_positions(kind, n, d)
+    npts = len(pos)
+    vol_per = {"cubic": d ** 3, "fcc": d ** 3 / math.sqrt(2.0), "hcp": d ** 3 / math.sqrt(2.0)}[kind]
+    rng = np.random.default_rng(seed)
+    st = _empty_state(npts)
+    st["x"], st["y"], st["z"] = pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy()
+    v = vel * rng.normal(size=(3, npts))
+    st["vx"], st["vy"], st["vz"] = v[0].copy(), v[1].copy(), v[2].copy()
+    st["m"][:] = vol_per
+    st["h"][:] = h
+    st["u"][:] = K / (Gamma - 1.0)
+    if solid:
+        st["type"][:] = 1
+        st["mu"][:] = 0.5
+        st["Y0"][:] = 0.1
+        st["eps_break"][:] = 0.05
+    eos = dict(K=np.array([K]), Gamma=np.array([Gamma]))
+    return st, eos
+
+
 def random_state(n: int, seed: int, box: float | None = None, h_lo: float = 0.5,
                  h_hi: float = 1.2, solid_frac: float = 0.5, vel: float = 0.05,
                  stress: float = 0.02, nstars: int = 1, lattice: bool = False,

@@ -10,7 +10,8 @@ import oracle
 from paper_2107_07315_gb300 import inputs as I
 from paper_2107_07315_gb300 import sph
 
-from _parity import TOL_FP64, TOL_MIXED, assert_close, assert_same_neighbors, gpu_rhs
+from _parity import (TOL_FP64, TOL_MIXED, assert_close, assert_same_neighbors, field_errors,
+                     gpu_rhs)
 
 pytestmark = pytest.mark.gpu
 MAT = dict(I.DEFAULT_MATERIAL)
@@ -176,3 +177,32 @@ def test_bad_arguments_rejected():
     bad["star"] = np.full(len(st["x"]), 3, np.int32)
     with pytest.raises(sph.SphError):
         sph.sph_init(sph.device_state(bad), eos, MAT, None, sph.SPH_MIXED)
+
+
+@pytest.mark.parametrize("prec,tol", PREC)
+@pytest.mark.parametrize("kind", ["cubic", "fcc", "hcp"])
+@pytest.mark.parametrize("h", [0.5, 0.5 * 2 ** 0.5])
+def test_lattice_shell_boundaries(prec, tol, kind, h):
+    # support 2h equal to the first (d = 1) or second (sqrt 2) shell distance:
+    # whole shells sit on the strict r < h_a + h_b boundary, where only the
+    # FP64 rounding of r^2 decides; lists must still equal the oracle's
+    st, eos = I.lattice_state(kind, n=7, d=1.0, h=h)
+    # h one ulp larger on a random half of the particles: pairs of two such
+    # particles reach just past the shell, the others stop just at it
+    pick = np.random.default_rng(3).random(len(st["h"])) < 0.5
+    st["h"][pick] *= 1.0 + 2e-16
+    if h > 0.6:
+        _check(st, eos, prec=prec, tol=tol, label="lattice %s h=%g" % (kind, h))
+        return
+    # support 2h = d: every neighbour sits at q = r/h_ab ~ 2 where W and grad W
+    # vanish like (2 - q)^2, so the pair forces are rounding noise (~1e-31) in
+    # any precision; the lists and the density (self term) are what is defined
+    o = oracle.rhs(st, eos, MAT, None, scales=True)
+    g, ctx, _ = gpu_rhs(st, eos, MAT, None, prec)
+    offs, idx = oracle.neighbors(st)
+    assert_same_neighbors(ctx, offs, idx)
+    assert offs[-1] > 0
+    errs = field_errors(g, o)
+    for k in ("D", "rho", "P", "cs"):
+        assert errs[k] <= tol[k], (k, errs[k])
+    assert np.array_equal(g["ncount"], o["ncount"])

@@ -604,3 +604,24 @@ def test_tov_pieces_matches_theta_form_and_balances():
         den = rho * (1 + u + P / rho) / (al * al)
         acc = oracle.tejeda_accel(al, ga, q, gq, np.zeros(3), np.array([dPdr / den, 0, 0]), 0.0)
         assert abs(acc[0]) < 2e-3 * abs(al * ga[0] / q), (frac, acc[0])
+
+
+# ---------------------------------------------------------------- lattices
+@pytest.mark.parametrize("kind,first,second", [("cubic", 6, 18), ("fcc", 12, 18),
+                                              ("hcp", 12, 18)])
+def test_lattice_coordination(kind, first, second):
+    # interior sites: 12 nearest neighbours at d in fcc and hcp (6 in the
+    # cubic lattice); with the second shell (d sqrt 2 in fcc and hcp, d sqrt 2
+    # in the cubic lattice) 18 in all three
+    st, eos = I.lattice_state(kind, n=6, d=1.0, h=0.55)
+    pos = np.stack([st["x"], st["y"], st["z"]], 1)
+    c = pos.mean(0)
+    centre = int(np.argmin(((pos - c) ** 2).sum(1)))
+    offs, idx = oracle.neighbors(st, subset=np.array([centre]))
+    assert offs[1] - offs[0] == first
+    st["h"][:] = 0.5 * 1.42  # support 1.42 > sqrt(2)
+    offs, idx = oracle.neighbors(st, subset=np.array([centre]))
+    assert offs[1] - offs[0] == second
+    # the nearest distance is d
+    d = np.sqrt(((pos[idx] - pos[centre]) ** 2).sum(1))
+    assert abs(d.min() - 1.0) < 1e-12
