@@ -335,24 +335,37 @@ def _random_rotation(rng) -> np.ndarray:
                      [2*(b*d-a*c), 2*(c*d+a*b), a*a-b*b-c*c+d*d]])
 
 
-def place_star(prof: TovProfile, N: int, rng, jitter: float = 0.05) -> np.ndarray:
+def place_star(prof: TovProfile, N: int, rng, jitter: float = 0.05):
     """N equal-baryon-mass particles on concentric shells (Sec. II.A).
 
     Shell populations follow the cumulative baryon mass of rho psi^6; each
     shell is a Fibonacci sphere with a random rotation; radii carry a uniform
     relative jitter of +-``jitter`` of the local shell spacing.
     """
-    rb = prof.rbar
-    dens = prof.rho * prof.psi4 ** 1.5
+    return place_profile(prof.rbar, prof.rho * prof.psi4 ** 1.5, N, rng, jitter)
+
+
+def place_profile(rb, dens, N: int, rng, jitter: float = 0.05):
+    """N equal-mass particles on concentric Fibonacci shells following the
+    radial density dens(rb) (zero where no matter is); returns (positions,
+    particle mass).  Shells start where the density first becomes positive."""
+    rb = np.asarray(rb, np.float64)
+    dens = np.asarray(dens, np.float64)
     cum = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] * rb[1:] ** 2 + dens[:-1] * rb[:-1] ** 2)
                                             * np.diff(rb))]) * 4.0 * math.pi
     Mb = cum[-1]
     mp = Mb / N
     # shell edges: spacing (mp/dens)^(1/3) evaluated at the shell's inner edge
-    edges = [0.0]
+    first = int(np.argmax(dens > 0))
+    edges = [float(rb[max(first - 1, 0)])]
     while True:
         r0 = edges[-1]
         d = np.interp(r0, rb, dens)
+        if d <= 0 and r0 <= rb[first]:
+            # an inner edge where the matter only begins: size the first shell
+            # by the mean density over one spacing at the peak density
+            s0 = (mp / dens.max()) ** (1.0 / 3.0)
+            d = float(np.mean(np.interp(np.linspace(r0, r0 + s0, 16), rb, dens)))
         if d <= 0:
             break
         s = (mp / d) ** (1.0 / 3.0)
@@ -542,6 +555,63 @@ def relax_state(N: int, seed: int = 1, Gamma_r: float = 1.01, jitter: float = 0.
     ext = relax_external([prof], [(0.0, 0.0, 0.0)], eos_r, nr=nr,
                          damping=damping_per_crossing * cs / prof.rbar_s)
     return st, eos_r, ext, eos, prof
+
+
+# ---------------------------------------------------------------------------
+# Elastic shell in an external potential (the crust-shell experiment, Sec. III)
+# ---------------------------------------------------------------------------
+def shell_state(N: int, r_in: float = 0.6, r_out: float = 1.0, rho0: float = 1.0,
+                K: float = 0.5, Gamma: float = 2.0, shear: float = 0.1, seed: int = 1,
+                nr: int = 2048, damping: float = 0.0):
+    """A shell of matter between r_in and r_out with density
+    rho_t = rho0 sin(pi (r - r_in)/(r_out - r_in)), held by the external
+    potential of its own profile (as in the relaxation, Sec. II.A) and solid
+    with shear modulus mu = shear * rho0 c_s0^2 (c_s0^2 = Gamma K rho0^(Gamma-1)),
+    no yield and no breaking.  Returns (state, eos, external, info) with info
+    holding the mean density and radius and the thin-shell estimate of the l=2
+    toroidal frequency, omega^2 = (l-1)(l+2) mu / (rho R^2)."""
+    rng = np.random.default_rng(seed)
+    rb = np.linspace(0.0, r_out, 8 * nr)
+    dens = np.where((rb > r_in) & (rb < r_out),
+                    rho0 * np.sin(math.pi * (rb - r_in) / (r_out - r_in)), 0.0)
+    pos, mp = place_profile(rb, dens, N, rng, jitter=0.05)
+    n = len(pos)
+    st = _empty_state(n)
+    st["x"], st["y"], st["z"] = pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy()
+    st["m"][:] = mp
+    st["h"][:] = smoothing_lengths(pos, 60)
+    r = np.sqrt((pos ** 2).sum(1))
+    rho = np.interp(r, rb, dens)
+    st["u"][:] = K * np.maximum(rho, 1e-3 * rho0) ** (Gamma - 1.0) / (Gamma - 1.0)
+    cs0 = math.sqrt(Gamma * K * rho0 ** (Gamma - 1.0))
+    mu = shear * rho0 * cs0 * cs0
+    st["type"][:] = 1
+    st["mu"][:] = mu
+    st["Y0"][:] = 1e30
+    st["eps_break"][:] = 1e30
+    eos = dict(K=np.array([K]), Gamma=np.array([Gamma]))
+    # external field of the shell's own profile (floored at 1 % of rho0)
+    grid = np.linspace(0.0, r_out, nr)
+    rho_t = np.maximum(np.interp(grid, rb, dens), 0.01 * rho0)
+    phi = -K * Gamma * rho_t ** (Gamma - 1.0) / (Gamma - 1.0)
+    ext = dict(kind=1, nr=nr, r_max=np.array([r_out]), g=(-np.gradient(phi, grid, edge_order=2))[None, :],
+               center=np.zeros((1, 3)), r_wall=np.array([r_out]),
+               k_wall=10.0 * cs0 * cs0 / (r_out - r_in) ** 2, damping=float(damping))
+    mass = 4.0 * math.pi * np.trapezoid(dens * rb ** 2, rb)
+    rho_mean = mass / (4.0 / 3.0 * math.pi * (r_out ** 3 - r_in ** 3))
+    R_mean = float(np.trapezoid(dens * rb ** 3, rb) / np.trapezoid(dens * rb ** 2, rb))
+    omega = math.sqrt(4.0 * mu / (rho_mean * R_mean ** 2))
+    info = dict(mu=mu, cs0=cs0, rho_mean=rho_mean, R_mean=R_mean, omega_thin=omega)
+    return st, eos, ext, info
+
+
+def toroidal_l2_velocity(st: dict, amp: float, R: float):
+    """Axisymmetric l=2 toroidal velocity, v = amp (r/R) sin(theta) cos(theta) phi_hat
+    (v proportional to r_hat x grad Y_2^0): in Cartesian form amp z (-y, x, 0)/(r R)."""
+    x, y, z = st["x"], st["y"], st["z"]
+    r = np.sqrt(x * x + y * y + z * z)
+    f = amp * z / (np.where(r > 0, r, 1.0) * R)
+    return -f * y, f * x, np.zeros_like(z)
 
 
 def cfl_dt(state: dict, eos: dict, C: float = 0.3) -> float:

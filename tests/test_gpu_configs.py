@@ -1,5 +1,6 @@
 """Workload-level GPU checks: batched star ensemble, radial-mode frequency of
-mixed vs FP64 runs, crust yield/damage flags, autotuned lanes."""
+mixed vs FP64 runs and of solid vs fluid crusts, crust yield/damage flags,
+autotuned lanes, quadrupole-mode frequency."""
 import math
 
 import numpy as np
@@ -208,3 +209,21 @@ def test_quadrupole_mode_frequency_mixed_vs_fp64():
     amp = np.abs(q64 - q64.mean()).max()
     assert amp > 0.0
     assert np.abs(q32 - q64).max() < 1e-2 * amp + 1e-9 * np.abs(q64).max()
+
+
+def test_radial_mode_solid_crust_equals_fluid_crust():
+    # Sec. V: the l=0 oscillation of a star with a solid crust matches the same
+    # star with a fluid crust, since mu << B (here mu = 0.01 P, B = Gamma P)
+    st, eos, met, prof = I.star_state(20000, seed=1, amp_l0=1e-2, crust_frac=0.3,
+                                      mu_over_P=0.01)
+    assert (st["type"] == 1).sum() > 0.15 * len(st["x"])
+    fl = {k: v.copy() for k, v in st.items()}
+    fl["type"][:] = 0
+    dt = I.cfl_dt(st, eos)
+    t, r_s = _central_density_series(st, eos, met, sph.SPH_MIXED, dt, 1200, 10)
+    _, r_f = _central_density_series(fl, eos, met, sph.SPH_MIXED, dt, 1200, 10)
+    w_s, w_f = _fit_frequency(t, r_s), _fit_frequency(t, r_f)
+    # measured: frequencies equal to 5e-6, series within 1 % of the amplitude
+    assert abs(w_s / w_f - 1.0) < 5e-4, (w_s, w_f)
+    amp = np.abs(r_f - r_f.mean()).max()
+    assert np.abs(r_s - r_f).max() < 0.03 * amp
