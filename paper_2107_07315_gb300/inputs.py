@@ -422,6 +422,15 @@ def _sph_coords(pos):
     return r, cth, sth, phi
 
 
+def dYl0_dtheta(l: int, cth, sth):
+    """d/dtheta of the orthonormal Y_l^0 = sqrt((2l+1)/(4 pi)) P_l(cos theta):
+    -sin(theta) sqrt((2l+1)/(4 pi)) P_l'(cos theta)."""
+    c = np.zeros(l + 1)
+    c[l] = 1.0
+    dP = np.polynomial.legendre.legval(cth, np.polynomial.legendre.legder(c))
+    return -sth * math.sqrt((2 * l + 1) / (4.0 * math.pi)) * dP
+
+
 def _empty_state(n: int) -> dict:
     z = np.zeros(n)
     return dict(x=z.copy(), y=z.copy(), z=z.copy(), vx=z.copy(), vy=z.copy(), vz=z.copy(),
@@ -434,13 +443,15 @@ def star_state(N: int, Gamma: float = 2.0, seed: int = 1, crust_frac: float = 0.
                mu_over_P: float = 0.01, Y0: float = 0.1, eps_break: float = 0.05,
                amp_l0: float = 1e-3, amp_l2: float = 0.0, M: float = 1.4, R_km: float = 12.0,
                Y0_over_mu=None, nr: int = 4096, n_target: int = 60, center=(0.0, 0.0, 0.0),
-               prof: TovProfile | None = None):
+               prof: TovProfile | None = None, modes=()):
     """One star: (state, eos, metric, profile).
 
     Crust = particles beyond (1 - crust_frac) of the isotropic surface radius,
     solid with mu = mu_over_P * P(r), Y0, eps_break per particle.  Velocity
     perturbations (Sec. II.B): v_r = amp_l0 c_s sin(pi r/R) and
     v_theta = amp_l2 c_s sin(pi r/R) d/dtheta Y_2^0, c_s relativistic.
+    modes: further (l, n, amp) terms v_theta += amp c_s sin(n pi r/R) d/dtheta Y_l^0
+    (the paper's (delta v_theta)_nl0 with the m = 0 harmonic).
     """
     rng = np.random.default_rng(seed)
     if prof is None:
@@ -468,6 +479,8 @@ def star_state(N: int, Gamma: float = 2.0, seed: int = 1, crust_frac: float = 0.
     vr = amp_l0 * cs * sinr
     # d/dtheta Y_2^0 = sqrt(5/(16 pi)) * (-6 cos sin)
     vth = amp_l2 * cs * sinr * math.sqrt(5.0 / (16.0 * math.pi)) * (-6.0 * cth * sth)
+    for l, nrad, amp in modes:
+        vth = vth + amp * cs * np.sin(nrad * math.pi * np.minimum(r, Rs) / Rs) * dYl0_dtheta(l, cth, sth)
     er = pos / np.where(r > 0, r, 1.0)[:, None]
     eth = np.stack([cth * np.cos(phi), cth * np.sin(phi), -sth], axis=1)
     v = vr[:, None] * er + vth[:, None] * eth
