@@ -135,8 +135,10 @@ constexpr int kRoundsD = 4;  // phase-1 rounds per block, density kernels
 constexpr int kRoundsF = 2;  // phase-1 rounds per block, force kernels
 
 // ------------------------------------------------------------------ density
+// 12 blocks per SM (at most 40 registers): the 1e5-particle star's 1563
+// blocks then fit in one wave; at 44 registers they took two.
 template <int LPI, int R>
-__global__ void __launch_bounds__(kTB)
+__global__ void __launch_bounds__(kTB, 12)
 k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRates out, int cap)
 {
     constexpr int PB = kTB / LPI * R;  // particles per block
