@@ -280,7 +280,8 @@ def run_ours(args):
     dstate, dbuf, step_bytes = sph.device_state_packed(st, dev)
     torch.cuda.synchronize()
     ctx = sph.sph_init(dstate, eos, I.DEFAULT_MATERIAL, met, prec,
-                       dict(h_nmin=55, h_nmax=65, use_graph=1), stream=stream.cuda_stream)
+                       dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=args.sort_every),
+                       stream=stream.cuda_stream)
     if external is not None:
         sph.sph_set_external(ctx, external)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -341,7 +342,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     e2e_pairs = float(sph.sph_stats(ctx)[1] - p_before)
-    launches = int(stats1[3]) * args.steps
+    launches = int(stats1[12] - stats0[12])
 
     # aggregate over ranks: total pairs, max time
     if ws > 1:
@@ -385,6 +386,7 @@ def run_ours(args):
             "n_particles": n,
             "pairs_per_step": pairs_step,
             "stars_per_gpu": nst,
+            "sort_every": args.sort_every,
             "l2": "flushed between timed steps by a 256 MB write outside the events",
             "parallelism": "independent star per GPU" if ws > 1 else "single GPU",
         },
@@ -398,12 +400,24 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)},
         "clocks": clocks,
     }
+    if ws == 1 and args.sort_every > 1:
+        # the same protocol with a curve sort on every step, for comparison
+        c1 = sph.sph_init(dstate, eos, I.DEFAULT_MATERIAL, met, prec,
+                          dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=1),
+                          stream=stream.cuda_stream)
+        if external is not None:
+            sph.sph_set_external(c1, external)
+        t1, p1 = time_steps(c1, dt, args.steps, 3, flush, stream)
+        sph.sph_free(c1)
+        out["sort_every_1"] = {"value": p1 / (t1 * 1e-3), "unit": "pairs/s",
+                               "ms_per_step": t1 / args.steps}
     if ws == 1 and args.fp64_steps > 0 and prec == sph.SPH_MIXED:
         # the plain FP64 GPU path on the same star, same step and flush protocol
         d64 = sph.device_state(st, dev)
         torch.cuda.synchronize()
         c64 = sph.sph_init(d64, eos, I.DEFAULT_MATERIAL, met, sph.SPH_FP64,
-                           dict(h_nmin=55, h_nmax=65, use_graph=1), stream=stream.cuda_stream)
+                           dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=args.sort_every),
+                           stream=stream.cuda_stream)
         if external is not None:
             sph.sph_set_external(c64, external)
         t64, p64 = time_steps(c64, dt, args.fp64_steps, 3, flush, stream)
@@ -680,6 +694,8 @@ def main():
                     help="timed steps of the plain FP64 path on the same star (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count-solid", type=int, default=1)
+    ap.add_argument("--sort-every", type=int, default=8,
+                    help="curve sort every k steps (tree and lists are rebuilt every step)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

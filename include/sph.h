@@ -141,13 +141,20 @@ typedef struct {
  * kernels [0: 8]; -1 lets sph_init time both on the bound state and keep
  * the faster (the summation order then depends on that timing).
  * use_graph: capture each step in a CUDA graph [1].
- * totals_every: compute totals every k steps inside sph_step [0: never]. */
+ * totals_every: compute totals every k steps inside sph_step [0: never].
+ * sort_every: sph_step sorts the particles along the space-filling curve on
+ * steps 0, k, 2k, ... (counted by the step counter) and keeps the last
+ * sort's order on the others; every step still rebuilds the tree and the
+ * neighbour lists from the current positions, so the lists are the same
+ * sets (only the order of pair sums, hence rounding, depends on k)
+ * [0 or 1: every step].  sph_rhs always sorts. */
 typedef struct {
     int32_t h_nmin, h_nmax;
     int32_t max_neighbors;
     int32_t lanes_per_particle;
     int32_t use_graph;
     int32_t totals_every;
+    int32_t sort_every;
 } sph_options;
 
 /* Create a context bound to the particle buffers.  Validates the inputs,
@@ -190,10 +197,12 @@ sph_status sph_totals(sph_ctx *ctx, double out[16]);
 
 /* Counters (host out[16]): 0 ordered neighbour pairs of the last right-hand
  * side, 1 pairs summed over all right-hand sides, 2 right-hand sides
- * evaluated, 3 kernel launches in one step, 4 tree leaves, 5 marginal pairs
+ * evaluated, 3 kernel launches in the last step, 4 tree leaves, 5 marginal pairs
  * re-checked in FP64 (cumulative), 6 neighbour capacity per particle,
  * 7 lanes per particle, 8 1 if steps run as a CUDA graph, 9 steps taken,
- * 10 radix passes, 11 cell bits per axis of the curve key.  Synchronous. */
+ * 10 radix passes, 11 cell bits per axis of the curve key, 12 kernel
+ * launches issued by sph_step (cumulative), 13 steps per curve sort.
+ * Synchronous. */
 sph_status sph_stats(sph_ctx *ctx, int64_t out[16]);
 
 /* Device-time measurement with CUDA events on the context's stream.
@@ -207,7 +216,8 @@ sph_status sph_timing(sph_ctx *ctx, int32_t enable);
 sph_status sph_timing_read(sph_ctx *ctx, double out[12]);
 
 /* Checkpoint: the bound particle state plus the rates carried between steps,
- * flags and the step counter, as an opaque host blob.  sph_state_size gives
+ * flags, the step counter and the particle order of the last curve sort, as
+ * an opaque host blob.  sph_state_size gives
  * its size; sph_get_state writes it; sph_set_state restores it so that
  * continuing reproduces an uninterrupted run bit for bit.  Synchronous. */
 sph_status sph_state_size(sph_ctx *ctx, int64_t *bytes);

@@ -73,12 +73,14 @@ struct sph_ctx {
     int have_rates = 0;
     int64_t steps = 0;
     int launches_per_step = 0;
-    // graph
-    cudaGraph_t graph = nullptr;       // kept alive: its nodes name the timing events
-    cudaGraphExec_t gexec = nullptr;
-    double gdt = 0.0;
-    int gtiming = 0;
-    cudaGraphNode_t gev_nodes[EV_N] = {};
+    int64_t launches_total = 0;        // kernel launches issued by sph_step
+    // graphs of a step: [0] keeps the last sort's order, [1] sorts again
+    cudaGraph_t graph[2] = {};         // kept alive: their nodes name the timing events
+    cudaGraphExec_t gexec[2] = {};
+    double gdt[2] = {};
+    int gtiming[2] = {};
+    int glaunches[2] = {};
+    cudaGraphNode_t gev_nodes[2][EV_N] = {};
     // timing
     int timing = 0;
     std::vector<TimingSlot> slots;
@@ -293,12 +295,12 @@ void rec(sph_ctx *c, cudaEvent_t ev, bool capturing)
 
 // The right-hand side on the given velocity and stress, into `out`.
 void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool capturing,
-                 int *nlaunch)
+                 int *nlaunch, bool resort = true)
 {
     if (c->n == 0) return;
     rec(c, slot_ev(c, EV_BUILD), capturing);
     launch_build(st, c->s, c->plan, c->tl, c->nleaves, c->cap, c->prec == SPH_FP64, c->stream,
-                 nlaunch, slot_ev(c, EV_LISTS), capturing ? 1 : 0);
+                 nlaunch, slot_ev(c, EV_LISTS), capturing ? 1 : 0, resort);
     rec(c, slot_ev(c, EV_DENSITY), capturing);
     launch_density(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
                    c->stream);
@@ -309,13 +311,13 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
     if (nlaunch) *nlaunch += 2;
 }
 
-void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch)
+void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch, bool resort)
 {
     StepState ss = step_state_of(c);
     rec(c, slot_ev(c, EV_STEP), capturing);
     launch_kick_drift(ss, c->r, dt, c->stream);
     DevState st = state_of(c, c->vp, c->vp + c->n, c->vp + 2 * c->n, c->Sp);
-    enqueue_rhs(c, st, c->r, capturing, nlaunch);
+    enqueue_rhs(c, st, c->r, capturing, nlaunch, resort);
     launch_kick_return(ss, c->r, eos_of(c), c->mat, dt, c->opt.h_nmin, c->opt.h_nmax, c->stream);
     rec(c, slot_ev(c, EV_STEP_END), capturing);
     if (nlaunch) *nlaunch += 2;
@@ -366,17 +368,31 @@ sph_status autotune_lanes(sph_ctx *c)
     return SPH_OK;
 }
 
-void drop_graph(sph_ctx *c)
+void drop_graph(sph_ctx *c, int k)
 {
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->gexec = nullptr;
-    c->graph = nullptr;
+    if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+    if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+    c->gexec[k] = nullptr;
+    c->graph[k] = nullptr;
 }
 
-sph_status capture_step(sph_ctx *c, double dt)
+void drop_graph(sph_ctx *c)
 {
-    drop_graph(c);
+    drop_graph(c, 0);
+    drop_graph(c, 1);
+}
+
+// Whether step number k (counted from the context's creation) sorts the
+// particles along the curve again.
+bool resort_at(const sph_ctx *c, int64_t k)
+{
+    return c->opt.sort_every <= 1 || k % c->opt.sort_every == 0;
+}
+
+sph_status capture_step(sph_ctx *c, double dt, bool resort)
+{
+    const int g = resort ? 1 : 0;
+    drop_graph(c, g);
     cudaGraph_t graph = nullptr;
     // Timing slot 0's events mark the nodes; replays swap in the slot's events.
     int saved_used = c->slot_used;
@@ -385,16 +401,16 @@ sph_status capture_step(sph_ctx *c, double dt)
     }
     CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int nl = 0;
-    enqueue_step(c, dt, true, &nl);
+    enqueue_step(c, dt, true, &nl, resort);
     cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
     if (e != cudaSuccess) return fail(SPH_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    e = cudaGraphInstantiate(&c->gexec[g], graph, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
-        c->gexec = nullptr;
+        c->gexec[g] = nullptr;
         return fail(SPH_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     }
-    for (int k = 0; k < EV_N; ++k) c->gev_nodes[k] = nullptr;
+    for (int k = 0; k < EV_N; ++k) c->gev_nodes[g][k] = nullptr;
     if (c->timing) {
         size_t nn = 0;
         cudaGraphGetNodes(graph, nullptr, &nn);
@@ -407,13 +423,13 @@ sph_status capture_step(sph_ctx *c, double dt)
             cudaEvent_t ev;
             cudaGraphEventRecordNodeGetEvent(nd, &ev);
             for (int k = 0; k < EV_N; ++k)
-                if (ev == c->slots[saved_used].ev[k]) c->gev_nodes[k] = nd;
+                if (ev == c->slots[saved_used].ev[k]) c->gev_nodes[g][k] = nd;
         }
     }
-    c->graph = graph;
-    c->gdt = dt;
-    c->gtiming = c->timing;
-    c->launches_per_step = nl;
+    c->graph[g] = graph;
+    c->gdt[g] = dt;
+    c->gtiming[g] = c->timing;
+    c->glaunches[g] = nl;
     return SPH_OK;
 }
 
@@ -460,6 +476,7 @@ sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_materi
             return fail(SPH_ERR_ARG, "lanes_per_particle must be -1, 0, 4 or 8");
         if (opt->h_nmax < 0 || opt->h_nmin < 0 || (opt->h_nmax > 0 && opt->h_nmin > opt->h_nmax))
             return fail(SPH_ERR_ARG, "h_nmin/h_nmax band invalid");
+        if (opt->sort_every < 0) return fail(SPH_ERR_ARG, "sort_every must be >= 0");
     }
     return SPH_OK;
 }
@@ -638,7 +655,8 @@ int64_t state_blob_size(const sph_ctx *c)
 {
     // header (8 int64) + doubles: x y z vx vy vz u h mu Y0 eps (11n) + S (6n)
     // + rates ax ay az dudt (4n) + dS (6n) + type, flags (2n bytes)
-    return 64 + 8 * (27 * c->n) + 2 * c->n;
+    // + the particle order of the last sort (4n bytes)
+    return 64 + 8 * (27 * c->n) + 2 * c->n + 4 * c->n;
 }
 
 }  // namespace
@@ -716,20 +734,25 @@ sph_status sph_step(sph_ctx *c, double dt, int32_t nsteps)
             STATUS_TRY(ensure_slot(c));
             c->slot_kind_step = 1;
         }
+        const bool resort = resort_at(c, c->steps);
+        const int g = resort ? 1 : 0;
         if (graph) {
-            if (!c->gexec || c->gdt != dt || c->gtiming != c->timing) STATUS_TRY(capture_step(c, dt));
+            if (!c->gexec[g] || c->gdt[g] != dt || c->gtiming[g] != c->timing)
+                STATUS_TRY(capture_step(c, dt, resort));
             if (c->timing) {
                 for (int e = 0; e < EV_N; ++e)
-                    if (c->gev_nodes[e])
-                        CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->gev_nodes[e],
-                                                                      c->slots[c->slot_used].ev[e]));
+                    if (c->gev_nodes[g][e])
+                        CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(
+                            c->gexec[g], c->gev_nodes[g][e], c->slots[c->slot_used].ev[e]));
             }
-            CUDA_TRY(cudaGraphLaunch(c->gexec, c->stream));
+            CUDA_TRY(cudaGraphLaunch(c->gexec[g], c->stream));
+            c->launches_per_step = c->glaunches[g];
         } else {
             int nl = 0;
-            enqueue_step(c, dt, false, &nl);
+            enqueue_step(c, dt, false, &nl, resort);
             c->launches_per_step = nl;
         }
+        c->launches_total += c->launches_per_step;
         if (c->timing) c->slot_used++;
         c->steps++;
         if (c->opt.totals_every > 0 && c->steps % c->opt.totals_every == 0) {
@@ -884,6 +907,8 @@ sph_status sph_stats(sph_ctx *c, int64_t out[16])
     out[9] = c->steps;
     out[10] = c->plan.passes;
     out[11] = c->plan.key_bits_axis;
+    out[12] = c->launches_total;
+    out[13] = c->opt.sort_every > 1 ? c->opt.sort_every : 1;
     return SPH_OK;
 }
 
@@ -957,6 +982,7 @@ sph_status sph_get_state(sph_ctx *c, void *host_buf, int64_t bytes)
     STATUS_TRY(get(c->r.dS, 6 * d));
     STATUS_TRY(get(c->P.type, n));
     STATUS_TRY(get(c->P.flags, n));
+    STATUS_TRY(get(c->s.perm, 4 * (size_t)n));
     return SPH_OK;
 }
 
@@ -984,6 +1010,12 @@ sph_status sph_set_state(sph_ctx *c, const void *host_buf, int64_t bytes)
     STATUS_TRY(put(c->r.dS, 6 * d));
     STATUS_TRY(put(c->P.type, n));
     STATUS_TRY(put(c->P.flags, n));
+    // the order of the last sort: the steps that keep it sum pairs in the
+    // same order as the run that wrote the checkpoint
+    const int32_t *perm = (const int32_t *)p;
+    for (int64_t i = 0; i < n; ++i)
+        if (perm[i] < 0 || perm[i] >= n) return fail(SPH_ERR_ARG, "checkpoint order out of range");
+    STATUS_TRY(put(c->s.perm, 4 * (size_t)n));
     c->steps = hdr[2];
     c->have_rates = (int)hdr[3];
     return SPH_OK;

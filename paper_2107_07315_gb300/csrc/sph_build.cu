@@ -407,7 +407,9 @@ __device__ __forceinline__ double float_to_double_exact(float f)
     return __longlong_as_double((long long)bits);
 }
 
-// Sorted copies and the FP32 j-record halves read by the list build.
+// Sorted copies and the FP32 j-record halves read by the list build.  order
+// may be perm itself (keeping the last sort's order): each thread reads and
+// rewrites only its own slot.
 __global__ void k_gather(DevState st, const uint32_t *order, DevScalars *sc, int32_t *perm,
                          double *xs, double *ys, double *zs, double *hs, uint8_t *tys,
                          float4 *rec, float4 *pos4, double4_32a *rec64)
@@ -798,7 +800,8 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
 // Host-side launch sequence of the neighbour search.
 void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
                   const TreeLevels &tl, int nleaves, int cap, int fp64_records,
-                  cudaStream_t stream, int *nlaunch, cudaEvent_t ev_lists, int ev_external)
+                  cudaStream_t stream, int *nlaunch, cudaEvent_t ev_lists, int ev_external,
+                  bool resort)
 {
     const bool multi_star = plan.star_bits > 0;
     const int64_t n = st.n;
@@ -809,24 +812,28 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     k_bbox<<<bblocks, kBoxThreads, 0, stream>>>(
         st, reinterpret_cast<unsigned long long *>(s.bbox_partial), s.bbox_done, s.sc, s.radix_tot);
     ++nl;
-    // keys, all digit histograms and cleared tile status words in one launch
-    unsigned long long *status = reinterpret_cast<unsigned long long *>(s.hist);
-    const int64_t status_words = (int64_t)plan.passes * plan.nblocks * 256;
-    int kb = (int)((n + kSortThreads - 1) / kSortThreads);
-    if (kb > 2 * kBoxBlocksMax) kb = 2 * kBoxBlocksMax;
-    k_keys_hist<<<kb, kSortThreads, 0, stream>>>(st, s.sc, plan.key_bits_axis, plan.passes,
-                                                 s.keys[0], s.vals[0], s.radix_tot, status,
-                                                 status_words);
-    ++nl;
-    for (int p = 0; p < plan.passes; ++p) {
-        int src = p & 1, dst = src ^ 1;
-        k_onesweep<<<plan.nblocks, kSortThreads, 0, stream>>>(
-            s.keys[src], s.vals[src], s.keys[dst], s.vals[dst], n, plan.ipt, 8 * p,
-            s.radix_tot + 256 * p, status + (int64_t)p * plan.nblocks * 256, &s.sc->tile_next[p],
-            s.sc);
+    // the order of the last sort (every entry of perm is a valid caller index)
+    const uint32_t *order = reinterpret_cast<const uint32_t *>(s.perm);
+    if (resort) {
+        // keys, all digit histograms and cleared tile status words in one launch
+        unsigned long long *status = reinterpret_cast<unsigned long long *>(s.hist);
+        const int64_t status_words = (int64_t)plan.passes * plan.nblocks * 256;
+        int kb = (int)((n + kSortThreads - 1) / kSortThreads);
+        if (kb > 2 * kBoxBlocksMax) kb = 2 * kBoxBlocksMax;
+        k_keys_hist<<<kb, kSortThreads, 0, stream>>>(st, s.sc, plan.key_bits_axis, plan.passes,
+                                                     s.keys[0], s.vals[0], s.radix_tot, status,
+                                                     status_words);
         ++nl;
+        for (int p = 0; p < plan.passes; ++p) {
+            int src = p & 1, dst = src ^ 1;
+            k_onesweep<<<plan.nblocks, kSortThreads, 0, stream>>>(
+                s.keys[src], s.vals[src], s.keys[dst], s.vals[dst], n, plan.ipt, 8 * p,
+                s.radix_tot + 256 * p, status + (int64_t)p * plan.nblocks * 256,
+                &s.sc->tile_next[p], s.sc);
+            ++nl;
+        }
+        order = s.vals[plan.passes & 1];
     }
-    const uint32_t *order = s.vals[plan.passes & 1];
     const int tb = 256;
     const int gb = (int)((n + tb - 1) / tb);
     k_gather<<<gb, tb, 0, stream>>>(st, order, s.sc, s.perm, s.xs, s.ys, s.zs, s.hs, s.tys, s.rec,

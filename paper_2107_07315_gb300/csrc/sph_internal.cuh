@@ -201,11 +201,14 @@ struct SortPlan {
 constexpr int kBoxBlocksMax = 304;
 
 // ev_lists (optional) is recorded between the tree and the neighbour-list
-// kernels; ev_external marks a record inside a stream capture.
+// kernels; ev_external marks a record inside a stream capture.  resort false
+// keeps the particle order of s.perm (the last sort) instead of sorting
+// along the curve again: the sorted copies, the tree and the lists are still
+// rebuilt from the current positions, so the lists are the same sets.
 void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
                   const TreeLevels &tl, int nleaves, int cap, int fp64_records,
                   cudaStream_t stream, int *nlaunch, cudaEvent_t ev_lists = nullptr,
-                  int ev_external = 0);
+                  int ev_external = 0, bool resort = true);
 
 void launch_density(const DevState &st, const Scratch &s, const DevEos &eos,
                     const DevMetric &g, const DevRates &out, int cap, int lanes, int fp64,

@@ -30,3 +30,30 @@ def test_packed_state_layout():
     # views alias the buffer: a write through the buffer shows in the field
     buf[f["u"].data_ptr() - base:f["u"].data_ptr() - base + 8] = 0
     assert f["u"][0].item() == 0.0
+
+
+def _c_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/sph.h, in order."""
+    import os
+    import re
+
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "sph.h")).read()
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", hdr)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = re.sub(r"/\*.*?\*/", "", decl, flags=re.S).strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            fields.append(re.sub(r"[^A-Za-z0-9_]", " ", part).split()[-1])
+    return fields
+
+
+def test_ctypes_structs_match_header():
+    # the binding's ctypes layouts name the C structs' fields in the same order
+    # (a field appended to the header and not to the binding shifts the rest)
+    for cls in (sph.sph_particles, sph.sph_eos, sph.sph_material, sph.sph_metric,
+                sph.sph_external, sph.sph_rates, sph.sph_options):
+        names = [f[0] for f in cls._fields_]
+        assert names == _c_struct_fields(cls.__name__), cls.__name__

@@ -111,11 +111,15 @@ def test_graph_replay_matches_direct_launches(prec):
 
 
 @pytest.mark.parametrize("prec", [sph.SPH_FP64, sph.SPH_MIXED])
-def test_checkpoint_resume_bit_exact(prec):
+@pytest.mark.parametrize("sort_every", [1, 3])
+def test_checkpoint_resume_bit_exact(prec, sort_every):
+    # with sort_every = 3 the resumed steps 2 and 4, 5 keep the order of the
+    # sorts at steps 0 and 3: the checkpoint carries that order
+    opts = dict(sort_every=sort_every)
     st, eos = I.random_state(2500, seed=6, vel=0.2, stress=0.05)
-    full, _, _ = _run(st, eos, None, MAT, prec, 1e-3, 6)
+    full, _, _ = _run(st, eos, None, MAT, prec, 1e-3, 6, opts)
     dev = sph.device_state(st)
-    ctx = _ctx(dev, eos, MAT, None, prec)
+    ctx = _ctx(dev, eos, MAT, None, prec, opts)
     sph.sph_step(ctx, 1e-3, 2)
     blob = sph.sph_get_state(ctx)
     # resume in a fresh context bound to fresh buffers
@@ -124,13 +128,37 @@ def test_checkpoint_resume_bit_exact(prec):
     st2["m"] = st["m"].copy()
     st2["star"] = st["star"].copy()
     dev2 = sph.device_state(st2)
-    ctx2 = _ctx(dev2, eos, MAT, None, prec)
+    ctx2 = _ctx(dev2, eos, MAT, None, prec, opts)
     sph.sph_set_state(ctx2, blob)
     sph.sph_step(ctx2, 1e-3, 4)
     sph.sph_sync(ctx2)
     res = sph.to_numpy(dev2)
     for k in KEYS + ("flags",):
         assert np.array_equal(res[k], full[k]), k
+
+
+@pytest.mark.parametrize("prec, rel", [(sph.SPH_FP64, 1e-12), (sph.SPH_MIXED, 2e-5)])
+def test_sort_every_keeps_lists_exact(prec, rel):
+    # steps 1-3 of sort_every = 4 keep the order of step 0's sort: the lists
+    # of step 1 (same positions in both runs) are the same sets, and nine
+    # steps differ from sorting every step by the rounding of the pair-sum
+    # order only; h follows the neighbour counts, so it stays bit-identical
+    st, eos, met, _ = I.star_state(8000, seed=3, amp_l0=0.02, amp_l2=0.02)
+    dt = I.cfl_dt(st, eos)
+    opts = lambda k: dict(h_nmin=55, h_nmax=65, sort_every=k)
+    _, c1, _ = _run(st, eos, met, MAT, prec, dt, 2, opts(1))
+    _, c4, _ = _run(st, eos, met, MAT, prec, dt, 2, opts(4))
+    o1, i1 = sph.neighbors(c1)
+    o4, i4 = sph.neighbors(c4)
+    assert np.array_equal(o1, o4) and np.array_equal(i1, i4)
+    assert sph.sph_stats(c4)[13] == 4
+    a, ca, _ = _run(st, eos, met, MAT, prec, dt, 9, opts(1))
+    b, cb, _ = _run(st, eos, met, MAT, prec, dt, 9, opts(4))
+    assert np.array_equal(a["h"], b["h"]) and np.array_equal(a["flags"], b["flags"])
+    _close(b, a, rel, keys=("x", "y", "z", "vx", "vy", "vz", "u"))
+    # the steps that keep the order launch fewer kernels (no keys, no radix passes)
+    la, lb = sph.sph_stats(ca)[12], sph.sph_stats(cb)[12]
+    assert lb < la
 
 
 def test_totals_match_oracle():
