@@ -285,12 +285,10 @@ def run_ours(args):
     if external is not None:
         sph.sph_set_external(ctx, external)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    sph.sph_timing(ctx, True)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             sph.sph_step(ctx, dt, 1)
         sph.sph_sync(ctx)
-    sph.sph_timing_read(ctx)  # discard warm-up samples
     stats0 = sph.sph_stats(ctx)
     uuid = None
     try:
@@ -308,9 +306,21 @@ def run_ours(args):
         dist.barrier()
     clocks = clk.stop()
     sph.sph_sync(ctx)
-    tim = sph.sph_timing_read(ctx)
     stats1 = sph.sph_stats(ctx)
     pairs = float(stats1[1] - stats0[1])
+    # per-kernel times: a separate pass whose step graph carries event nodes
+    # between the phases (the nodes cost time of their own, so the timed
+    # steps above run without them); a whole number of sort cycles
+    sph.sph_timing(ctx, True)
+    with torch.cuda.stream(stream):
+        sph.sph_step(ctx, dt, 1)  # captures the instrumented graph
+    sph.sph_sync(ctx)
+    sph.sph_timing_read(ctx)
+    k_steps = max(1, args.sort_every) * max(1, 16 // max(1, args.sort_every))
+    t_inst, _ = time_steps(ctx, dt, k_steps, 0, flush, stream)
+    sph.sph_sync(ctx)
+    tim = sph.sph_timing_read(ctx)
+    sph.sph_timing(ctx, False)
     # solid-pair share for the flop count (pairs touching a crust particle)
     pairs_step = float(stats1[0])
     solid_pairs = 0.0
@@ -320,7 +330,11 @@ def run_ours(args):
         cnt = np.diff(offs)
         owner = np.repeat(np.arange(n), cnt)
         solid_pairs = float(np.count_nonzero((ty[owner] == 1) | (ty[idx] == 1)))
-    sph.sph_timing(ctx, False)
+    # re-capture the plain step graphs (both sort phases) outside the e2e timing
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.sort_every)):
+            sph.sph_step(ctx, dt, 1)
+    sph.sph_sync(ctx)
 
     # end-to-end: the step's fields (positions, velocities, u, h, S, flags) live
     # in pinned host memory; every step copies them in, steps, copies them out
@@ -395,6 +409,8 @@ def run_ours(args):
         # the right-hand side alone (sort, tree, lists, density, force), from the
         # CUDA events inside the timed steps; the step adds both kicks
         "rhs_only": _rhs_only(tim, pairs_step),
+        # the instrumented pass that gave the per-kernel times
+        "instrumented_ms_per_step": t_inst / k_steps,
         "gpu_launches": launches,
         "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)},
@@ -407,10 +423,17 @@ def run_ours(args):
                           stream=stream.cuda_stream)
         if external is not None:
             sph.sph_set_external(c1, external)
-        t1, p1 = time_steps(c1, dt, args.steps, 3, flush, stream)
-        sph.sph_free(c1)
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                sph.sph_step(c1, dt, 1)
+        sph.sph_sync(c1)
+        l0 = int(sph.sph_stats(c1)[12])
+        t1, p1 = time_steps(c1, dt, args.steps, 0, flush, stream)
+        sph.sph_sync(c1)
         out["sort_every_1"] = {"value": p1 / (t1 * 1e-3), "unit": "pairs/s",
-                               "ms_per_step": t1 / args.steps}
+                               "ms_per_step": t1 / args.steps,
+                               "gpu_launches": int(sph.sph_stats(c1)[12]) - l0}
+        sph.sph_free(c1)
     if ws == 1 and args.fp64_steps > 0 and prec == sph.SPH_MIXED:
         # the plain FP64 GPU path on the same star, same step and flush protocol
         d64 = sph.device_state(st, dev)
