@@ -47,6 +47,10 @@ struct TimingSlot {
 struct sph_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // second stream of the mixed force pass (solid-block kernel) and the
+    // events that fork it from and join it to stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t n = 0;
     int nstars = 1;
     sph_precision prec = SPH_MIXED;
@@ -306,9 +310,10 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
                    c->stream);
     rec(c, slot_ev(c, EV_FORCE), capturing);
     launch_force(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
-                 c->stream);
+                 c->stream, c->side, c->ev_fork, c->ev_join);
     rec(c, slot_ev(c, EV_FORCE_END), capturing);
-    if (nlaunch) *nlaunch += 2;
+    // density, force (mixed precision: fluid-block and solid-block kernels)
+    if (nlaunch) *nlaunch += c->prec == SPH_FP64 ? 2 : 3;
 }
 
 void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch, bool resort)
@@ -345,7 +350,7 @@ sph_status autotune_lanes(sph_ctx *c)
             launch_density(st, c->s, eos_of(c), c->met, c->r, c->cap, lanes, c->prec == SPH_FP64,
                            c->stream);
             launch_force(st, c->s, eos_of(c), c->mat, c->met, c->r, c->cap, lanes,
-                         c->prec == SPH_FP64, c->stream);
+                         c->prec == SPH_FP64, c->stream, c->side, c->ev_fork, c->ev_join);
         }
         cudaEventRecord(e1, c->stream);
         float ms = 0.f;
@@ -497,6 +502,11 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : 256;
     c->lanes = c->opt.lanes_per_particle > 0 ? c->opt.lanes_per_particle : 8;
     c->stream = (cudaStream_t)stream;
+    if (prec == SPH_MIXED) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
     CUDA_TRY(cudaGetDevice(&c->device));
     const int64_t n = c->n;
     // Host copies of type and star: star layout, solid check.
@@ -1027,6 +1037,12 @@ void sph_free(sph_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     drop_graph(c);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto &s : c->slots)
         for (int e = 0; e < EV_N; ++e) cudaEventDestroy(s.ev[e]);
     for (void *p : c->allocs) cudaFree(p);

@@ -214,9 +214,14 @@ void launch_density(const DevState &st, const Scratch &s, const DevEos &eos,
                     const DevMetric &g, const DevRates &out, int cap, int lanes, int fp64,
                     cudaStream_t stream);
 
+// Mixed precision runs an all-fluid-block kernel and a solid-block kernel
+// over the same grid; with side, fork and join given, the solid-block kernel
+// runs on side (after fork is recorded on stream) so the two overlap, and
+// stream waits on join before it goes on.
 void launch_force(const DevState &st, const Scratch &s, const DevEos &eos,
                   const DevMaterial &mat, const DevMetric &g, const DevRates &out, int cap,
-                  int lanes, int fp64, cudaStream_t stream);
+                  int lanes, int fp64, cudaStream_t stream, cudaStream_t side = nullptr,
+                  cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 
 // Step kernels (sph_step.cu).
 struct StepState {

@@ -414,10 +414,13 @@ __device__ __forceinline__ void finalize(int64_t i, int c, int64_t N, const DevS
 enum { A_P0, A_P1, A_P2, A_X0, A_X1, A_X2, A_DU, A_DUC, A_DD, A_G00, A_G01, A_G02, A_G10, A_G11,
        A_G12, A_G20, A_G21, A_G22, A_N };
 
-// (6 blocks of 128 threads per SM: at most 85 registers, which keeps the
-// register allocation at 80 per thread)
-template <int LPI, int R>
-__global__ void __launch_bounds__(kTB, 6)
+// Two instantiations share the grid: SOLID = false takes the blocks whose
+// particles are all fluid (no stress of its own, no velocity gradient: fewer
+// live registers, 8 blocks of 128 threads per SM), SOLID = true the blocks
+// holding a solid particle (6 blocks per SM: at most 85 registers, which
+// keeps the allocation at 80).  Each returns at once on the other's blocks.
+template <int LPI, int R, bool SOLID>
+__global__ void __launch_bounds__(kTB, SOLID ? 6 : 8)
 k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
               DevRates out, int cap)
 {
@@ -426,6 +429,11 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
     __shared__ float s_acc[A_N][PB];
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
     const int64_t base = (int64_t)blockIdx.x * PB;
+    {
+        const int64_t ib = base + threadIdx.x;
+        const bool mine = threadIdx.x < PB && ib < n && s.tys[ib] == 1;
+        if ((__syncthreads_or(mine) != 0) != SOLID) return;
+    }
     const float alpha_av = (float)mat.alpha_av, beta_av = (float)mat.beta_av;
     const float eta2 = (float)mat.eta2;
 #pragma unroll 1
@@ -443,7 +451,7 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
             a1 = s.rec[n + i];
             a2 = s.rec[2 * n + i];
             a3 = s.rec[3 * n + i];
-            solid_i = s.tys[i] == 1;
+            solid_i = SOLID && s.tys[i] == 1;
             if (solid_i) {
                 as0 = s.sd2[i];
                 as1 = s.sd2[n + i];
@@ -533,7 +541,7 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
     const int star = st.star ? st.star[c] : 0;
     const float4 a2 = s.rec[2 * n + i];
     const float4 p0 = s.pp[i * 2 + 0], p1 = s.pp[i * 2 + 1];
-    const bool solid_i = s.tys[i] == 1;
+    const bool solid_i = SOLID && s.tys[i] == 1;
     float aP[3] = {s_acc[A_P0][t], s_acc[A_P1][t], s_acc[A_P2][t]};
     float aX[3] = {s_acc[A_X0][t], s_acc[A_X1][t], s_acc[A_X2][t]};
     float G[3][3] = {{s_acc[A_G00][t], s_acc[A_G01][t], s_acc[A_G02][t]},
@@ -689,7 +697,7 @@ void launch_density(const DevState &st, const Scratch &s, const DevEos &eos, con
 
 void launch_force(const DevState &st, const Scratch &s, const DevEos &eos, const DevMaterial &mat,
                   const DevMetric &g, const DevRates &out, int cap, int lanes, int fp64,
-                  cudaStream_t stream)
+                  cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     int64_t n = st.n;
     if (fp64) {
@@ -699,13 +707,29 @@ void launch_force(const DevState &st, const Scratch &s, const DevEos &eos, const
         else
             k_force_fp64<8, kRoundsF><<<(int)((n + pb_fp64<8>(kRoundsF) - 1) / pb_fp64<8>(kRoundsF)), kTB64, 0,
                                        stream>>>(n, st, s, eos, mat, g, out, cap);
+        return;
+    }
+    // all-fluid blocks on stream; blocks holding a solid particle (same grid)
+    // on side when given, so that the two kernels overlap
+    const bool fan = side && fork && join;
+    cudaStream_t s2 = stream;
+    if (fan) {
+        cudaEventRecord(fork, stream);
+        cudaStreamWaitEvent(side, fork, 0);
+        s2 = side;
+    }
+    if (lanes == 4) {
+        const int nb = (int)((n + pb_mixed<4>(kRoundsF) - 1) / pb_mixed<4>(kRoundsF));
+        k_force_mixed<4, kRoundsF, true><<<nb, kTB, 0, s2>>>(n, st, s, eos, mat, g, out, cap);
+        k_force_mixed<4, kRoundsF, false><<<nb, kTB, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
     } else {
-        if (lanes == 4)
-            k_force_mixed<4, kRoundsF><<<(int)((n + pb_mixed<4>(kRoundsF) - 1) / pb_mixed<4>(kRoundsF)), kTB, 0,
-                                        stream>>>(n, st, s, eos, mat, g, out, cap);
-        else
-            k_force_mixed<8, kRoundsF><<<(int)((n + pb_mixed<8>(kRoundsF) - 1) / pb_mixed<8>(kRoundsF)), kTB, 0,
-                                        stream>>>(n, st, s, eos, mat, g, out, cap);
+        const int nb = (int)((n + pb_mixed<8>(kRoundsF) - 1) / pb_mixed<8>(kRoundsF));
+        k_force_mixed<8, kRoundsF, true><<<nb, kTB, 0, s2>>>(n, st, s, eos, mat, g, out, cap);
+        k_force_mixed<8, kRoundsF, false><<<nb, kTB, 0, stream>>>(n, st, s, eos, mat, g, out, cap);
+    }
+    if (fan) {
+        cudaEventRecord(join, side);
+        cudaStreamWaitEvent(stream, join, 0);
     }
 }
 
