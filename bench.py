@@ -212,32 +212,38 @@ class ClockSampler:
                 "samples": len(sm), "source": "nvidia-smi, 200 ms period"}
 
 
+# the mixed force pass is two kernels (all-fluid blocks, blocks with a solid)
 PROFILE_FILES = {
-    "force": ("force_mixed_star1e5.md", "sph_pairs.cu"),
-    "density": ("density_mixed_star1e5.md", "sph_pairs.cu"),
-    "lists": ("neighbors_star1e5.md", "sph_build.cu"),
+    "force": (("force_mixed_fluid_star1e5.md", "force_mixed_solid_star1e5.md"), "sph_pairs.cu"),
+    "density": (("density_mixed_star1e5.md",), "sph_pairs.cu"),
+    "lists": (("neighbors_star1e5.md",), "sph_build.cu"),
 }
 
 
 def traffic_from_profile(key: str):
-    """DRAM bytes per launch from the committed ncu summary of that kernel,
-    or None when the kernel's source changed since the counters were taken."""
-    name, src = PROFILE_FILES[key]
-    path = os.path.join(ROOT, "profiles", name)
-    if not os.path.exists(path):
-        return None
+    """DRAM bytes per pass from the committed ncu summaries of its kernels,
+    or None when their source changed since the counters were taken."""
+    names, src = PROFILE_FILES[key]
     kernel_src = os.path.join(ROOT, "paper_2107_07315_gb300", "csrc", src)
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    src_ok, traffic = False, None
-    for line in open(path):
-        if line.startswith("kernel_source_sha256_16:") and line.split(":")[1].strip() == h:
-            src_ok = True
-        if line.startswith("dram_bytes_per_launch:"):
-            try:
-                traffic = float(line.split(":")[1].strip())
-            except ValueError:
-                traffic = None
-    return traffic if src_ok else None
+    total = 0.0
+    for name in names:
+        path = os.path.join(ROOT, "profiles", name)
+        if not os.path.exists(path):
+            return None
+        src_ok, traffic = False, None
+        for line in open(path):
+            if line.startswith("kernel_source_sha256_16:") and line.split(":")[1].strip() == h:
+                src_ok = True
+            if line.startswith("dram_bytes_per_launch:"):
+                try:
+                    traffic = float(line.split(":")[1].strip())
+                except ValueError:
+                    traffic = None
+        if not src_ok or traffic is None:
+            return None
+        total += traffic
+    return total
 
 
 def run_ours(args):
