@@ -158,8 +158,12 @@ k_density_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevR
         }
         float sum = 0.f, comp = 0.f;
         const int32_t *list = s.nbr + i * (int64_t)cap;
+        // the next list entry is loaded one iteration ahead, so the record
+        // loads of a pair do not wait on their index load
+        int jn = sub < cnt ? list[sub] : 0;
         for (int k = sub; k < cnt; k += LPI) {
-            int j = list[k];
+            int j = jn;
+            if (k + LPI < cnt) jn = list[k + LPI];
             float4 q0 = s.rec[j], q1 = s.rec[n + j];
             float dx = (a0.x - q0.x) + (a1.x - q1.x);
             float dy = (a0.y - q0.y) + (a1.y - q1.y);
@@ -462,8 +466,10 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
         float G00 = 0.f, G01 = 0.f, G02 = 0.f, G10 = 0.f, G11 = 0.f, G12 = 0.f, G20 = 0.f,
               G21 = 0.f, G22 = 0.f;
         const int32_t *list = s.nbr + i * (int64_t)cap;
+        int jn = sub < cnt ? list[sub] : 0;
         for (int k = sub; k < cnt; k += LPI) {
-            const int j = list[k];
+            const int j = jn;
+            if (k + LPI < cnt) jn = list[k + LPI];
             const float4 q0 = s.rec[j], q1 = s.rec[n + j];
             const float4 q2 = s.rec[2 * n + j], q3 = s.rec[3 * n + j];
             const bool solid_j = q3.w != 0.f;  // type rides in the record: no extra load
