@@ -192,6 +192,8 @@ def device_state(state: dict, device="cuda"):
 
 
 # Fields a step changes, first in the packed layout so that one copy moves them.
+# With the material option break_zero_S = 1 a step also zeroes mu of particles
+# that break; such callers move mu as well.
 STEP_KEYS = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "S", "flags")
 
 
