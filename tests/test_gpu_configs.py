@@ -35,6 +35,31 @@ def test_ensemble_batch_vs_oracle(ensemble, prec, tol):
     assert_close(g, o, tol, label="ensemble")
 
 
+def test_ensemble_sort_every_keeps_lists(ensemble):
+    # multi-star batch: steps that keep the last curve order (sort_every = 4)
+    # give the same lists as sorting every step, and states equal to rounding
+    st, eos, met, params = ensemble
+    dt = 0.5 * I.cfl_dt(st, eos)
+    res = []
+    for k in (1, 4):
+        dev = sph.device_state(st)
+        torch.cuda.synchronize()
+        ctx = sph.sph_init(dev, eos, MAT, met, sph.SPH_FP64,
+                           dict(h_nmin=55, h_nmax=65, sort_every=k), stream=stream().cuda_stream)
+        sph.sph_step(ctx, dt, 2)
+        sph.sph_sync(ctx)
+        lists = sph.neighbors(ctx)
+        sph.sph_step(ctx, dt, 5)
+        sph.sph_sync(ctx)
+        res.append((lists, sph.to_numpy(dev)))
+    (l1, a), (l4, b) = res
+    assert np.array_equal(l1[0], l4[0]) and np.array_equal(l1[1], l4[1])
+    assert np.array_equal(a["h"], b["h"])
+    for key in ("x", "vx", "u"):
+        scale = np.abs(a[key]).max() + 1e-300
+        assert np.abs(a[key] - b[key]).max() <= 1e-12 * scale, key
+
+
 def test_ensemble_steps_match_single_stars(ensemble):
     # stepping the batch equals stepping each star alone (FP64, to rounding)
     st, eos, met, params = ensemble
