@@ -24,6 +24,7 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr float kInvPiF = 0.318309886183790671538f;
+constexpr double kInvPi = 0.318309886183790671538;
 
 template <typename T>
 struct MetricPt {
@@ -251,8 +252,10 @@ k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRa
             double dx = a0.x - q0.x, dy = a0.y - q0.y, dz = a0.z - q0.z;
             double r = sqrt(dx * dx + dy * dy + dz * dz);
             double hab = 0.5 * (a0.w + q0.w);
-            double q = r / hab;
-            double sig = 1.0 / (kPi * hab * hab * hab);
+            // one division per pair: the FP64 pipe is narrow on this GPU
+            double hinv = 1.0 / hab;
+            double q = r * hinv;
+            double sig = kInvPi * hinv * hinv * hinv;
             double W;
             if (q < 1.0) W = sig * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
             else {
@@ -596,29 +599,35 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
             const bool solid_j = s.tys[j] == 1;
             double dx[3] = {a0.x - q0.x, a0.y - q0.y, a0.z - q0.z};
             double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-            double r = sqrt(r2);
             double hab = 0.5 * (a0.w + q0.w);
+            // W'(r)/r with one division and one reciprocal square root per
+            // pair (the FP64 pipe is narrow on this GPU):
+            //   q < 1: h^-5/pi (2.25 q - 3);  q >= 1: -0.75 h^-4/pi (2 - q)^2 / r
+            double hinv = 1.0 / hab;
             double gW = 0.0;
-            if (r > 0.0) {
-                double q = r / hab;
-                double sig = 1.0 / (kPi * hab * hab * hab);
-                double dW;
-                if (q < 1.0) dW = (sig / hab) * (-3.0 * q + 2.25 * q * q);
+            if (r2 > 0.0) {
+                double rinv = rsqrt(r2);
+                double q = r2 * rinv * hinv;
+                double h2 = hinv * hinv;
+                double s4 = kInvPi * h2 * h2;
+                if (q < 1.0) gW = s4 * hinv * (2.25 * q - 3.0);
                 else {
                     double tq = 2.0 - q;
-                    dW = -(sig / hab) * 0.75 * tq * tq;
+                    gW = -0.75 * s4 * tq * tq * rinv;
                 }
-                gW = dW / r;
             }
             double w = q1.x * gW;
             double dv[3] = {a1.y - q1.y, a1.z - q1.z, a1.w - q1.w};
             double vdx = dv[0] * dx[0] + dv[1] * dx[1] + dv[2] * dx[2];
             double Pi = 0.0;
             if (vdx < 0.0) {
-                double mu = hab * vdx / (r2 + mat.eta2 * hab * hab);
+                // mu = h vdx / den and Pi = (-alpha cbar mu + beta mu^2) / Dbar,
+                // over one common denominator den^2 Dbar
+                double den = r2 + mat.eta2 * hab * hab;
+                double hv = hab * vdx;
                 double cbar = 0.5 * (a2.w + q2.w);
                 double Dbar = 0.5 * (a2.x + q2.x);
-                Pi = (-mat.alpha_av * cbar * mu + mat.beta_av * mu * mu) / Dbar;
+                Pi = (-mat.alpha_av * cbar * hv * den + mat.beta_av * hv * hv) / (den * den * Dbar);
             }
             double fp = (a2.z + q2.z) * w, fv = Pi * w;
             for (int d = 0; d < 3; ++d) {
