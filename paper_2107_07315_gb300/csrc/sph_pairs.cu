@@ -250,7 +250,9 @@ k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRa
             double4_32a q0 = s.rec64[(int64_t)j * 3 + 0];
             double mj = s.rec64[(int64_t)j * 3 + 1].x;
             double dx = a0.x - q0.x, dy = a0.y - q0.y, dz = a0.z - q0.z;
-            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            // r from the reciprocal square root (coincident particles: r = 0)
+            double r = r2 > 0.0 ? r2 * rsqrt(r2) : 0.0;
             double hab = 0.5 * (a0.w + q0.w);
             // one division per pair: the FP64 pipe is narrow on this GPU
             double hinv = 1.0 / hab;
