@@ -728,7 +728,14 @@ k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, c
             int nh = __popc(any), rank = __popc(any & lt_mask);
             if (lv == 1) {
                 if (mine) {
-                    s_leaf[warp][ncand + rank] = make_int2(leaf_start[c0 + c], leaf_start[c0 + c + 1]);
+                    if (MULTI_STAR) {
+                        s_leaf[warp][ncand + rank] =
+                            make_int2(leaf_start[c0 + c], leaf_start[c0 + c + 1]);
+                    } else {  // one star: leaf l holds sorted slots [8l, min(8l + 8, n))
+                        const int lo = kLeaf * (c0 + c);
+                        s_leaf[warp][ncand + rank] =
+                            make_int2(lo, (int)min((int64_t)lo + kLeaf, n));
+                    }
                     s_mask[warp][ncand + rank] = (unsigned short)cm;
                 }
                 ncand += nh;
