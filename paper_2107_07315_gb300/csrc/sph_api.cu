@@ -1004,6 +1004,18 @@ sph_status sph_set_state(sph_ctx *c, const void *host_buf, int64_t bytes)
     const int64_t *hdr = (const int64_t *)host_buf;
     if (hdr[0] != 0x53504831 || hdr[1] != n || hdr[4] != c->nstars)
         return fail(SPH_ERR_ARG, "checkpoint does not match this context");
+    {
+        // the stored particle order (the blob's last 4n bytes) must be a
+        // permutation; checked before anything is copied
+        const int32_t *perm =
+            (const int32_t *)((const char *)host_buf + state_blob_size(c) - 4 * n);
+        std::vector<unsigned char> seen((size_t)n, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            if (perm[i] < 0 || perm[i] >= n || seen[(size_t)perm[i]])
+                return fail(SPH_ERR_ARG, "checkpoint order is not a permutation");
+            seen[(size_t)perm[i]] = 1;
+        }
+    }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     const char *p = (const char *)host_buf + 64;
     auto put = [&](void *dst, size_t sz) -> sph_status {
@@ -1020,11 +1032,8 @@ sph_status sph_set_state(sph_ctx *c, const void *host_buf, int64_t bytes)
     STATUS_TRY(put(c->r.dS, 6 * d));
     STATUS_TRY(put(c->P.type, n));
     STATUS_TRY(put(c->P.flags, n));
-    // the order of the last sort: the steps that keep it sum pairs in the
-    // same order as the run that wrote the checkpoint
-    const int32_t *perm = (const int32_t *)p;
-    for (int64_t i = 0; i < n; ++i)
-        if (perm[i] < 0 || perm[i] >= n) return fail(SPH_ERR_ARG, "checkpoint order out of range");
+    // the order of the last sort (checked above): the steps that keep it sum
+    // pairs in the same order as the run that wrote the checkpoint
     STATUS_TRY(put(c->s.perm, 4 * (size_t)n));
     c->steps = hdr[2];
     c->have_rates = (int)hdr[3];

@@ -161,6 +161,21 @@ def test_sort_every_keeps_lists_exact(prec, rel):
     assert lb < la
 
 
+def test_checkpoint_with_bad_order_is_rejected():
+    # the order stored in a checkpoint must be a permutation of the particles
+    st, eos = I.random_state(500, seed=8, vel=0.1)
+    dev = sph.device_state(st)
+    ctx = _ctx(dev, eos, MAT, None, sph.SPH_MIXED)
+    sph.sph_step(ctx, 1e-3, 1)
+    blob = sph.sph_get_state(ctx).copy()
+    n = len(st["x"])
+    perm = blob[-4 * n:].view(np.int32)
+    perm[1] = perm[0]
+    with pytest.raises(sph.SphError):
+        sph.sph_set_state(ctx, blob)
+    sph.sph_set_state(ctx, sph.sph_get_state(ctx))
+
+
 def test_totals_match_oracle():
     st, eos, _, _ = I.cube_state(n_side=10)
     g, ctx, _ = _run(st, eos, None, MAT, sph.SPH_FP64, 1e-3, 3)
