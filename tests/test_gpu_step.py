@@ -176,6 +176,31 @@ def test_checkpoint_with_bad_order_is_rejected():
     sph.sph_set_state(ctx, sph.sph_get_state(ctx))
 
 
+def test_host_round_trip_steps_equal_device_steps():
+    # the end-to-end loop (step fields copied in from pinned host memory and
+    # back out around every step, one copy each way through the packed
+    # layout) computes exactly what device-resident steps compute
+    st, eos, met, _ = I.star_state(6000, seed=12, amp_l0=0.02)
+    dt = I.cfl_dt(st, eos)
+    opts = dict(h_nmin=55, h_nmax=65, sort_every=4)
+    ref, _, _ = _run(st, eos, met, MAT, sph.SPH_MIXED, dt, 6, opts)
+    fields, buf, step_bytes = sph.device_state_packed(st)
+    ctx = _ctx(fields, eos, MAT, met, sph.SPH_MIXED, opts)
+    host = buf[:step_bytes].cpu().pin_memory()
+    dstep = buf[:step_bytes]
+    s = stream()
+    with torch.cuda.stream(s):
+        for _ in range(6):
+            dstep.copy_(host, non_blocking=True)
+            sph.sph_step(ctx, dt, 1)
+            host.copy_(dstep, non_blocking=True)
+    sph.sph_sync(ctx)
+    torch.cuda.synchronize()
+    got = sph.to_numpy(fields)
+    for k in KEYS + ("flags",):
+        assert np.array_equal(got[k], ref[k]), k
+
+
 def test_totals_match_oracle():
     st, eos, _, _ = I.cube_state(n_side=10)
     g, ctx, _ = _run(st, eos, None, MAT, sph.SPH_FP64, 1e-3, 3)
