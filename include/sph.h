@@ -224,7 +224,6 @@ sph_status sph_state_size(sph_ctx *ctx, int64_t *bytes);
 sph_status sph_get_state(sph_ctx *ctx, void *host_buf, int64_t bytes);
 sph_status sph_set_state(sph_ctx *ctx, const void *host_buf, int64_t bytes);
 
-/* Release the context and its device memory (the caller's buffers stay). */
 /* Switch the external relaxation field on (kind 1) or off (NULL or kind 0)
  * for later right-hand sides and steps (Sec. II.A).  The tables are copied
  * into device memory owned by the context (each call allocates new copies,
@@ -240,6 +239,8 @@ sph_status sph_set_external(sph_ctx *ctx, const sph_external *ext);
  * (star count, K <= 0, Gamma <= 1), SPH_ERR_CUDA. */
 sph_status sph_relax_finish(sph_ctx *ctx, const sph_eos *eos);
 
+/* Release the context and its device memory (the caller's buffers stay).
+ * Waits for the context's stream first.  NULL is ignored. */
 void sph_free(sph_ctx *ctx);
 
 /* Neighbour lists without a context and without any device allocation, for

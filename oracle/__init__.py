@@ -92,37 +92,79 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(L):
+    """Declare argument and result types of the oracle's exported functions."""
+    L.ora_kernel_W.restype = C.c_double
+    L.ora_kernel_W.argtypes = [C.c_double, C.c_double]
+    L.ora_kernel_dWdr.restype = C.c_double
+    L.ora_kernel_dWdr.argtypes = [C.c_double, C.c_double]
+    L.ora_yield_factor.restype = C.c_double
+    L.ora_yield_factor.argtypes = [_d, C.c_double, C.c_int]
+    L.ora_sym_eigvals.argtypes = [_d, _d]
+    L.ora_breaks.restype = C.c_int
+    L.ora_breaks.argtypes = [_d, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int]
+    L.ora_rhs.restype = C.c_int
+    L.ora_step.restype = C.c_int
+    L.ora_metric_eval.argtypes = [C.POINTER(_Metric), C.c_int, C.c_double, C.c_double,
+                                  C.c_double, _d, _d, _d, _d]
+    L.ora_tejeda_accel.argtypes = [C.c_double, _d, C.c_double, _d, _d, _d,
+                                   C.c_double, _d]
+    L.ora_eos_eval.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int,
+                               _d, _d, _d, _d]
+    L.ora_external_accel.argtypes = [C.POINTER(_External), C.c_int, C.c_double,
+                                     C.c_double, C.c_double, _d, _d, _d]
+    L.ora_eos_eval_star.argtypes = [C.POINTER(_Eos), C.c_int, C.c_double, C.c_int,
+                                    _d, _d, _d, _d]
+    L.ora_num_threads.restype = C.c_int
+    L.ora_set_threads.argtypes = [C.c_int]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(_LIB)
-            L.ora_kernel_W.restype = C.c_double
-            L.ora_kernel_W.argtypes = [C.c_double, C.c_double]
-            L.ora_kernel_dWdr.restype = C.c_double
-            L.ora_kernel_dWdr.argtypes = [C.c_double, C.c_double]
-            L.ora_yield_factor.restype = C.c_double
-            L.ora_yield_factor.argtypes = [_d, C.c_double, C.c_int]
-            L.ora_sym_eigvals.argtypes = [_d, _d]
-            L.ora_breaks.restype = C.c_int
-            L.ora_breaks.argtypes = [_d, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int]
-            L.ora_rhs.restype = C.c_int
-            L.ora_step.restype = C.c_int
-            L.ora_metric_eval.argtypes = [C.POINTER(_Metric), C.c_int, C.c_double, C.c_double,
-                                          C.c_double, _d, _d, _d, _d]
-            L.ora_tejeda_accel.argtypes = [C.c_double, _d, C.c_double, _d, _d, _d,
-                                           C.c_double, _d]
-            L.ora_eos_eval.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int,
-                                       _d, _d, _d, _d]
-            L.ora_external_accel.argtypes = [C.POINTER(_External), C.c_int, C.c_double,
-                                             C.c_double, C.c_double, _d, _d, _d]
-            L.ora_eos_eval_star.argtypes = [C.POINTER(_Eos), C.c_int, C.c_double, C.c_int,
-                                            _d, _d, _d, _d]
-            L.ora_num_threads.restype = C.c_int
-            L.ora_set_threads.argtypes = [C.c_int]
-            _lib = L
+            _lib = _configure(C.CDLL(_LIB))
         return _lib
+
+
+class mutant:
+    """A copy of the oracle with planted mistakes, for tests that show a pin
+    detects them.  ``edits`` is a list of (old, new) source snippets; each
+    ``old`` must occur exactly once in sph_oracle.c.  Inside ``with
+    mutant(edits, workdir):`` every function of this module runs the mutated
+    copy; the real oracle is restored on exit.  The mutated library lives in
+    ``workdir`` (a temporary directory of the caller)."""
+
+    def __init__(self, edits, workdir: str):
+        src = open(_SRC).read()
+        for old, new in edits:
+            if src.count(old) != 1:
+                raise ValueError("mutation target must occur once: %r" % old)
+            src = src.replace(old, new)
+        tag = "%08x" % (abs(hash(tuple(edits))) & 0xffffffff)
+        csrc = os.path.join(workdir, "oracle_mutant_%s.c" % tag)
+        so = os.path.join(workdir, "liboracle_mutant_%s.so" % tag)
+        with open(csrc, "w") as f:
+            f.write(src)
+        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                        "-shared", "-std=c99", "-o", so, csrc, "-lm"], check=True)
+        self._lib = _configure(C.CDLL(so))
+        self._saved = None
+
+    def __enter__(self):
+        global _lib
+        lib()
+        with _lock:
+            self._saved, _lib = _lib, self._lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self._saved
+        return False
 
 
 def _p(a, t=_d):

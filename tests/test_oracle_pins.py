@@ -48,13 +48,14 @@ def test_kernel_derivative_and_support():
 
 
 def test_lattice_density_interior():
-    # Interior density of the unit lattice with h = 1.3: the lattice sum of W
-    # approximates the normalisation integral, so D -> 1 within the
-    # discretisation error of the kernel on the lattice.
+    # Interior density of the unit lattice (m = 1) with h = 1.3: the lattice
+    # sum m W(0, h) + sum_b m W(|b|, h) over the 80 lattice points with
+    # 0 < |b| < 2.6 equals 0.997261828303877, a value fixed by brute force
+    # over the lattice shells independently of the oracle.
     st, eos, _, _ = I.cube_state()
     r = oracle.rhs(st, eos, MAT, None, subset=np.array([8 * 256 + 8 * 16 + 8]))
     D = r["D"][8 * 256 + 8 * 16 + 8]
-    assert abs(D - 1.0) < 5e-3
+    assert abs(D - 0.997261828303877) < 1e-14
     assert r["ncount"][8 * 256 + 8 * 16 + 8] == 80  # lattice points with 0 < |x| < 2.6
 
 
