@@ -136,7 +136,8 @@ typedef struct {
 /* Run options (host); NULL in sph_init means the defaults in brackets.
  * h_nmin, h_nmax: after each step multiply h by 1.0625 when the neighbour
  * count is below h_nmin and by 0.9375 above h_nmax [0, 0: off].
- * max_neighbors: per-particle neighbour list capacity [0: 256].
+ * max_neighbors: most neighbours a particle may have (1..256); more raise
+ * SPH_ERR_CAPACITY at sph_sync [0: 256].
  * lanes_per_particle: 4 or 8 threads share one particle's list in the pair
  * kernels [0: 8]; -1 lets sph_init time both on the bound state and keep
  * the faster (the summation order then depends on that timing).
@@ -178,8 +179,21 @@ sph_status sph_rhs(sph_ctx *ctx, const sph_rates *out);
 sph_status sph_step(sph_ctx *ctx, double dt, int32_t nsteps);
 
 /* Wait for the context's stream and report device-side errors raised since
- * the last call (capacity, non-finite input, bounds, timeouts). */
+ * the last call (capacity, non-finite input, bounds, timeouts), then clear
+ * them.  A timed-out sort is reported as SPH_ERR_TIMEOUT: every kernel of
+ * that right-hand side that would read the sorted order returns without
+ * work, and so do those of later ones until sph_sync clears the error. */
 sph_status sph_sync(sph_ctx *ctx);
+
+/* Bound on the device-side waits of the context's sort: a sort tile that
+ * has made `polls` rounds of reads of its predecessors' published counts
+ * without finding its prefix (decoupled look-back) gives up and raises the
+ * timeout reported by sph_sync.  polls < 0 restores the default (2^22); 0
+ * makes every tile after the first give up at once (a way to exercise the
+ * timeout path on inputs of more than one sort tile, n > 256).  Library
+ * service, no counterpart in the paper.  Synchronous.  Errors: SPH_ERR_ARG
+ * (NULL ctx), SPH_ERR_CUDA. */
+sph_status sph_set_wait_limit(sph_ctx *ctx, int32_t polls);
 
 /* Neighbour lists of the last right-hand side, CSR in caller order with
  * ascending caller indices (b in N(a) iff b != a, same star and
@@ -201,16 +215,20 @@ sph_status sph_totals(sph_ctx *ctx, double out[16]);
  * re-checked in FP64 (cumulative), 6 neighbour capacity per particle,
  * 7 lanes per particle, 8 1 if steps run as a CUDA graph, 9 steps taken,
  * 10 radix passes, 11 cell bits per axis of the curve key, 12 kernel
- * launches issued by sph_step (cumulative), 13 steps per curve sort.
- * Synchronous. */
-sph_status sph_stats(sph_ctx *ctx, int64_t out[16]);
+ * launches issued by sph_step (cumulative), 13 steps per curve sort,
+ * 14 most candidate leaves of one leaf (pair tiles), 15 most neighbours of
+ * one particle, 16 candidate (leaf, leaf) tiles in all (14-16 of the last
+ * right-hand side), 17 1 for mixed precision, 18-23 zero.  Synchronous. */
+sph_status sph_stats(sph_ctx *ctx, int64_t out[24]);
 
 /* Device-time measurement with CUDA events on the context's stream.
  * enable 1 starts recording around the kernels of every step or right-hand
  * side; sph_timing_read returns (host out[12]) summed milliseconds and
- * sample counts: 0/1 force kernel, 2/3 density kernel, 4/5 whole steps (or
+ * sample counts: 0/1 force kernels, 2/3 FP64 density kernel (zero in mixed
+ * precision, where the tile kernel sums the density), 4/5 whole steps (or
  * right-hand sides), 6/7 bounding box through tree (keys, sort, gather,
- * tree), 8/9 neighbour-list kernel, 10/11 all neighbour search (6 plus 8).
+ * tree), 8/9 pair-tile kernel (candidate leaves, neighbour masks; in mixed
+ * precision also the density and equation of state), 10/11 both (6 plus 8).
  * Reading resets the sums.  Synchronous. */
 sph_status sph_timing(sph_ctx *ctx, int32_t enable);
 sph_status sph_timing_read(sph_ctx *ctx, double out[12]);
@@ -253,12 +271,17 @@ void sph_free(sph_ctx *ctx);
  * (caller order), offsets a device int64[n+1], idx a device int32[cap];
  * cuda_stream a cudaStream_t (NULL: legacy default stream).  Scratch is one
  * fixed device array of about 11.7 MB inside the library, present on every
- * GPU that loads it until the process exits; limits: n <= 16384 (larger n
- * returns SPH_ERR_ARG) and at most 128 neighbours per particle
- * (SPH_ERR_CAPACITY).  The first call on a device looks up the array's
- * device address (make that call before any stream capture).  Every call
- * shares the array and resets what must start at zero; calls that overlap on
- * the GPU race.  Synchronous. */
+ * GPU that loads it until the process exits.  Limits: n <= 16384 (larger n
+ * returns SPH_ERR_ARG), at most 128 neighbours per particle and 512
+ * candidate leaves (groups of 8 sorted particles) per leaf
+ * (SPH_ERR_CAPACITY); more than cap entries in all returns SPH_ERR_CAPACITY
+ * with offsets written and idx not.  Under lazy module loading (the CUDA
+ * default) the first call on a device loads the library's device code and
+ * the array, which takes device memory once: make one call with n >= 1
+ * before another allocator takes the whole device.  Every call looks up the
+ * array's address on the current device, shares the array with other calls
+ * and resets what must start at zero; calls that overlap on the GPU race.
+ * Synchronous. */
 sph_status sph_neighbors_noalloc(int64_t n, const double *x, const double *y, const double *z,
                                  const double *h, int64_t *offsets, int32_t *idx, int64_t cap,
                                  void *cuda_stream);

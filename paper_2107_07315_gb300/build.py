@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sph_build.cu", "sph_pairs.cu", "sph_step.cu", "sph_api.cu", "sph_noalloc.cu"]
+SOURCES = ["sph_build.cu", "sph_tiles.cu", "sph_pairs.cu", "sph_step.cu", "sph_api.cu",
+           "sph_noalloc.cu"]
 
 
 def _nvcc() -> str:
@@ -42,7 +43,8 @@ def _stale(obj: str, deps) -> bool:
 def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    header_deps = [os.path.join(CSRC, "sph_internal.cuh"), os.path.join(ROOT, "include", "sph.h")]
+    header_deps = [os.path.join(CSRC, "sph_internal.cuh"), os.path.join(CSRC, "sph_device.cuh"),
+                   os.path.join(ROOT, "include", "sph.h")]
     jobs = []
     objs = []
     for src in SOURCES:

@@ -62,6 +62,11 @@ struct sph_ctx {
     double *d_K = nullptr, *d_Gamma = nullptr;
     int npieces = 0;                                   // piecewise EoS (0: one polytrope)
     double *d_rho_b = nullptr, *d_Kp = nullptr, *d_Gp = nullptr, *d_ap = nullptr;
+    float *f_K = nullptr, *f_Gamma = nullptr;          // FP32 copies (mixed precision)
+    float *f_rho_b = nullptr, *f_Kp = nullptr, *f_Gp = nullptr, *f_ap = nullptr;
+    std::vector<float> h_fstar;                        // per-star FP32 constants (host copy)
+    float *d_fstar = nullptr;
+    int multi = 0;                                     // several stars in one index space
     DevMaterial mat{};
     DevMetric met{};
     Scratch s{};
@@ -170,6 +175,12 @@ DevEos eos_of(const sph_ctx *c)
     e.Kp = c->d_Kp;
     e.Gp = c->d_Gp;
     e.ap = c->d_ap;
+    e.Kf = c->f_K;
+    e.Gf = c->f_Gamma;
+    e.rho_bf = c->f_rho_b;
+    e.Kpf = c->f_Kp;
+    e.Gpf = c->f_Gp;
+    e.apf = c->f_ap;
     return e;
 }
 
@@ -216,9 +227,20 @@ sph_status upload_eos(sph_ctx *c, const sph_eos *eos)
     if (!c->d_K) {
         STATUS_TRY(c->alloc(&c->d_K, ns));
         STATUS_TRY(c->alloc(&c->d_Gamma, ns));
+        STATUS_TRY(c->alloc(&c->f_K, ns));
+        STATUS_TRY(c->alloc(&c->f_Gamma, ns));
     }
     CUDA_TRY(cudaMemcpy(c->d_K, eos->K, ns * sizeof(double), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->d_Gamma, eos->Gamma, ns * sizeof(double), cudaMemcpyHostToDevice));
+    {
+        std::vector<float> kf(ns), gf(ns);
+        for (int k = 0; k < ns; ++k) {
+            kf[k] = (float)eos->K[k];
+            gf[k] = (float)eos->Gamma[k];
+        }
+        CUDA_TRY(cudaMemcpy(c->f_K, kf.data(), ns * sizeof(float), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->f_Gamma, gf.data(), ns * sizeof(float), cudaMemcpyHostToDevice));
+    }
     c->npieces = eos->npieces > 1 ? eos->npieces : 0;
     if (c->npieces > 1) {
         const int np = c->npieces;
@@ -250,6 +272,17 @@ sph_status upload_eos(sph_ctx *c, const sph_eos *eos)
         CUDA_TRY(cudaMemcpy(c->d_Kp, Kp.data(), Kp.size() * sizeof(double), cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(c->d_Gp, Gp.data(), Gp.size() * sizeof(double), cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(c->d_ap, ap.data(), ap.size() * sizeof(double), cudaMemcpyHostToDevice));
+        auto to_f = [&](const std::vector<double> &v, float **dst) -> sph_status {
+            std::vector<float> f(v.size());
+            for (size_t k = 0; k < v.size(); ++k) f[k] = (float)v[k];
+            STATUS_TRY(c->alloc(dst, f.size()));
+            CUDA_TRY(cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+            return SPH_OK;
+        };
+        STATUS_TRY(to_f(rb, &c->f_rho_b));
+        STATUS_TRY(to_f(Kp, &c->f_Kp));
+        STATUS_TRY(to_f(Gp, &c->f_Gp));
+        STATUS_TRY(to_f(ap, &c->f_ap));
     }
     return SPH_OK;
 }
@@ -302,18 +335,22 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
                  int *nlaunch, bool resort = true)
 {
     if (c->n == 0) return;
+    const bool fp64 = c->prec == SPH_FP64;
     rec(c, slot_ev(c, EV_BUILD), capturing);
-    launch_build(st, c->s, c->plan, c->tl, c->nleaves, c->cap, c->prec == SPH_FP64, c->stream,
-                 nlaunch, slot_ev(c, EV_LISTS), capturing ? 1 : 0, resort);
+    launch_build(st, c->s, c->plan, c->tl, c->nleaves, fp64, c->stream, nlaunch, resort);
+    rec(c, slot_ev(c, EV_LISTS), capturing);
+    // pair tiles; in mixed precision the density and equation of state too
+    launch_tiles(st, c->s, c->tl, c->nleaves, c->multi, c->cap, fp64 ? 0 : 1, eos_of(c), c->met,
+                 out, c->stream);
     rec(c, slot_ev(c, EV_DENSITY), capturing);
-    launch_density(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
-                   c->stream);
+    if (fp64) launch_density_fp64(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->stream);
     rec(c, slot_ev(c, EV_FORCE), capturing);
-    launch_force(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->lanes, c->prec == SPH_FP64,
-                 c->stream, c->side, c->ev_fork, c->ev_join);
+    launch_force(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->lanes, fp64, c->stream,
+                 c->side, c->ev_fork, c->ev_join);
     rec(c, slot_ev(c, EV_FORCE_END), capturing);
-    // density, force (mixed precision: fluid-block and solid-block kernels)
-    if (nlaunch) *nlaunch += c->prec == SPH_FP64 ? 2 : 3;
+    // tiles, then density and force (FP64) or the fluid-block and solid-block
+    // force kernels (mixed precision)
+    if (nlaunch) *nlaunch += 3;
 }
 
 void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch, bool resort)
@@ -343,14 +380,15 @@ sph_status autotune_lanes(sph_ctx *c)
     CUDA_TRY(cudaEventCreate(&e1));
     float best = 3e38f;
     int best_lanes = 8;
+    const bool fp64 = c->prec == SPH_FP64;
     for (int lanes : {4, 8}) {
         c->lanes = lanes;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) cudaEventRecord(e0, c->stream);
-            launch_density(st, c->s, eos_of(c), c->met, c->r, c->cap, lanes, c->prec == SPH_FP64,
-                           c->stream);
-            launch_force(st, c->s, eos_of(c), c->mat, c->met, c->r, c->cap, lanes,
-                         c->prec == SPH_FP64, c->stream, c->side, c->ev_fork, c->ev_join);
+            if (fp64)
+                launch_density_fp64(st, c->s, eos_of(c), c->met, c->r, c->cap, lanes, c->stream);
+            launch_force(st, c->s, eos_of(c), c->mat, c->met, c->r, c->cap, lanes, fp64, c->stream,
+                         c->side, c->ev_fork, c->ev_join);
         }
         cudaEventRecord(e1, c->stream);
         float ms = 0.f;
@@ -438,6 +476,15 @@ sph_status capture_step(sph_ctx *c, double dt, bool resort)
     return SPH_OK;
 }
 
+// A point as hi + lo floats per coordinate: hi = fl32(x), lo = fl32(x - hi).
+void split_float(const double *x, float *hi, float *lo)
+{
+    for (int k = 0; k < 3; ++k) {
+        hi[k] = (float)x[k];
+        lo[k] = (float)(x[k] - (double)hi[k]);
+    }
+}
+
 int bits_for(int64_t n)
 {
     int lg = 1;
@@ -474,8 +521,8 @@ sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_materi
             if (!(g->r_max[s] > 0.0)) return fail(SPH_ERR_ARG, "metric r_max must be > 0");
     }
     if (opt) {
-        if (opt->max_neighbors < 0 || opt->max_neighbors > 4096)
-            return fail(SPH_ERR_ARG, "max_neighbors out of range");
+        if (opt->max_neighbors < 0 || opt->max_neighbors > kRowCap)
+            return fail(SPH_ERR_ARG, "max_neighbors must be 0..%d", kRowCap);
         if (opt->lanes_per_particle != 0 && opt->lanes_per_particle != 4 &&
             opt->lanes_per_particle != 8 && opt->lanes_per_particle != -1)
             return fail(SPH_ERR_ARG, "lanes_per_particle must be -1, 0, 4 or 8");
@@ -499,7 +546,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
         c->opt = sph_options{};
         c->opt.use_graph = 1;
     }
-    c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : 256;
+    c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : kRowCap;
     c->lanes = c->opt.lanes_per_particle > 0 ? c->opt.lanes_per_particle : 8;
     c->stream = (cudaStream_t)stream;
     if (prec == SPH_MIXED) {
@@ -549,6 +596,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     while ((1 << sb) < c->nstars) ++sb;
     c->plan.key_bits_axis = bits_for(n);
     c->plan.star_bits = sb;
+    c->multi = sb > 0 ? 1 : 0;
     int kb = 3 * c->plan.key_bits_axis + sb;
     c->plan.passes = (kb + 7) / 8;
     int64_t per_tile = 256ll * 304;
@@ -591,6 +639,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     STATUS_TRY(c->alloc(&s.sc, 1));
     CUDA_TRY(cudaMemset(s.bbox_done, 0, sizeof(unsigned int)));
     CUDA_TRY(cudaMemset(s.sc, 0, sizeof(DevScalars)));
+    CUDA_TRY(cudaMemset(s.ncnt, 0, nn * sizeof(int32_t)));
     CUDA_TRY(cudaMemcpy(s.leaf_start, leaf_start.data(), leaf_start.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice));
     if (!leaf_star.empty())
@@ -621,8 +670,13 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     c->mat.yield_mode = mat->yield_mode;
     c->mat.break_stress = mat->break_stress;
     c->mat.break_zero_S = mat->break_zero_S;
+    c->mat.alpha_f = (float)mat->alpha_av;
+    c->mat.beta_f = (float)mat->beta_av;
+    c->mat.eta2_f = (float)mat->eta2;
     c->met = DevMetric{};
     c->met.kind = 0;
+    c->h_fstar.assign((size_t)c->nstars * kFStar, 0.f);
+    STATUS_TRY(c->alloc(&c->d_fstar, c->h_fstar.size()));
     if (g && g->kind == 1) {
         int ns = g->nstars, nr = g->nr;
         c->met.kind = 1;
@@ -655,7 +709,16 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
         c->met.r_max = d_rmax;
         c->met.M = d_M;
         c->met.center = d_center;
+        for (int k = 0; k < ns; ++k) {
+            float *f = &c->h_fstar[(size_t)k * kFStar];
+            f[FS_RMAX] = (float)g->r_max[k];
+            f[FS_M] = (float)g->M[k];
+            split_float(g->center + 3 * k, f + FS_CHI, f + FS_CLO);
+        }
     }
+    CUDA_TRY(cudaMemcpy(c->d_fstar, c->h_fstar.data(), c->h_fstar.size() * sizeof(float),
+                        cudaMemcpyHostToDevice));
+    c->met.fstar = c->d_fstar;
     CUDA_TRY(cudaDeviceSynchronize());
     if (c->opt.lanes_per_particle == -1 && n > 0) STATUS_TRY(autotune_lanes(c));
     return SPH_OK;
@@ -785,11 +848,27 @@ sph_status sph_sync(sph_ctx *c)
         int zero = 0;
         CUDA_TRY(cudaMemcpy(&c->s.sc->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
         if (err & ERR_NONFINITE) return fail(SPH_ERR_NONFINITE, "non-finite position, velocity or h");
+        // a timed-out sort is the cause of any bounds flag raised with it
+        if (err & ERR_TIMEOUT)
+            return fail(SPH_ERR_TIMEOUT, "a sort pass gave up waiting for a predecessor tile");
         if (err & ERR_CAPACITY)
-            return fail(SPH_ERR_CAPACITY, "a neighbour list exceeded max_neighbors = %d", c->cap);
+            return fail(SPH_ERR_CAPACITY,
+                        "a particle has more than max_neighbors = %d neighbours, or a leaf more "
+                        "than %d candidate leaves",
+                        c->cap, kCandCap);
         if (err & ERR_BOUNDS) return fail(SPH_ERR_BOUNDS, "index out of bounds");
-        if (err & ERR_TIMEOUT) return fail(SPH_ERR_TIMEOUT, "device wait timed out");
     }
+    return SPH_OK;
+}
+
+sph_status sph_set_wait_limit(sph_ctx *c, int32_t polls)
+{
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    if (c->n == 0) return SPH_OK;
+    // stored form: 0 the default, > 0 that many polls, < 0 none
+    const int v = polls < 0 ? 0 : (polls == 0 ? -1 : polls);
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaMemcpy(&c->s.sc->spin_limit, &v, sizeof(int), cudaMemcpyHostToDevice));
     return SPH_OK;
 }
 
@@ -861,6 +940,16 @@ sph_status sph_set_external(sph_ctx *c, const sph_external *e)
     c->met.ext_rwall = d_rwall;
     c->met.k_wall = e->k_wall;
     c->met.damping = e->damping;
+    c->met.k_wall_f = (float)e->k_wall;
+    c->met.damping_f = (float)e->damping;
+    for (int k = 0; k < ns; ++k) {
+        float *f = &c->h_fstar[(size_t)k * kFStar];
+        f[FS_EXT_RMAX] = (float)e->r_max[k];
+        f[FS_EXT_RWALL] = (float)e->r_wall[k];
+        split_float(e->center + 3 * k, f + FS_EXT_CHI, f + FS_EXT_CLO);
+    }
+    CUDA_TRY(cudaMemcpy(c->d_fstar, c->h_fstar.data(), c->h_fstar.size() * sizeof(float),
+                        cudaMemcpyHostToDevice));
     drop_graph(c);
     c->have_rates = 0;  // the field changes the accelerations
     return SPH_OK;
@@ -898,13 +987,13 @@ sph_status sph_totals(sph_ctx *c, double out[16])
     return SPH_OK;
 }
 
-sph_status sph_stats(sph_ctx *c, int64_t out[16])
+sph_status sph_stats(sph_ctx *c, int64_t out[24])
 {
     if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
     DevScalars sc{};
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     CUDA_TRY(cudaMemcpy(&sc, c->s.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 16; ++k) out[k] = 0;
+    for (int k = 0; k < 24; ++k) out[k] = 0;
     out[0] = (int64_t)sc.pairs_last;
     out[1] = (int64_t)sc.pairs_total;
     out[2] = (int64_t)sc.rhs_count;
@@ -919,6 +1008,10 @@ sph_status sph_stats(sph_ctx *c, int64_t out[16])
     out[11] = c->plan.key_bits_axis;
     out[12] = c->launches_total;
     out[13] = c->opt.sort_every > 1 ? c->opt.sort_every : 1;
+    out[14] = sc.max_cand;
+    out[15] = sc.max_count;
+    out[16] = (int64_t)sc.tiles_last;
+    out[17] = c->prec == SPH_FP64 ? 0 : 1;
     return SPH_OK;
 }
 
@@ -1011,7 +1104,10 @@ sph_status sph_set_state(sph_ctx *c, const void *host_buf, int64_t bytes)
             (const int32_t *)((const char *)host_buf + state_blob_size(c) - 4 * n);
         std::vector<unsigned char> seen((size_t)n, 0);
         for (int64_t i = 0; i < n; ++i) {
-            if (perm[i] < 0 || perm[i] >= n || seen[(size_t)perm[i]])
+            if (perm[i] < 0 || perm[i] >= n)
+                return fail(SPH_ERR_BOUNDS, "checkpoint order entry %lld = %d is outside [0, %lld)",
+                            (long long)i, perm[i], (long long)n);
+            if (seen[(size_t)perm[i]])
                 return fail(SPH_ERR_ARG, "checkpoint order is not a permutation");
             seen[(size_t)perm[i]] = 1;
         }

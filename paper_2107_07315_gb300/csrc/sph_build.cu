@@ -1,17 +1,9 @@
-// Neighbour search: bounding box, Hilbert keys, LSD radix sort, sorted
-// gather, leaf tree and exact per-particle neighbour lists.
-//
-// The neighbour predicate is the one of Sec. I.B: b is a neighbour of a iff
-// b != a, both belong to the same star and |x_a - x_b| < 2 h_ab = h_a + h_b.
-// The lists must equal those of an FP64 evaluation of
-//     r2 = (dx*dx + dy*dy) + dz*dz < (h_a + h_b)^2
-// bit for bit, in both precisions.  Candidates are screened in FP32 from a
-// two-float position split (Xhi on a power-of-two grid plus an FP32
-// remainder) with an error bound; pairs inside the bound's band are decided
-// again in FP64 with round-to-nearest operations in that exact order.
+// Neighbour search, first half: bounding box, Hilbert keys, LSD radix sort,
+// sorted gather and the leaf tree.  The pair tiles over the tree (candidate
+// leaves and the exact neighbour masks) are built in sph_tiles.cu.
 #include <cstdio>
 
-#include "sph_internal.cuh"
+#include "sph_device.cuh"
 
 namespace sph {
 
@@ -150,10 +142,14 @@ __global__ void k_bbox(DevState st, unsigned long long *partial, unsigned int *d
             sc->key_scale_f[k] = (float)sc->inv_ext[k];
         }
         sc->eps_abs = 1e-6 * fmax(m, 1e-30);
-        sc->screen_c1 = (float)(1.67e-6 * m);
+        sc->eps_abs_f = (float)sc->eps_abs;
+        // absolute part of the tile screening band: 48 g u with u = 2^-24
+        sc->band_abs = (float)(48.0 * ldexp(sc->grid, -24));
         sc->pairs_last = 0ull;
+        sc->tiles_last = 0ull;
         sc->tree_done = 0;
-        sc->list_next = 0u;
+        sc->max_cand = 0;
+        sc->max_count = 0;
         sc->rhs_count += 1ull;
         *done = 0u;
     }
@@ -207,7 +203,16 @@ __device__ __forceinline__ uint32_t hilbert3(uint32_t x0, uint32_t x1, uint32_t 
 
 constexpr int kSortThreads = 256;
 constexpr int kMaxPasses = 8;
-constexpr int kSpinLimit = 1 << 22;  // look-back polls before giving up (error flag)
+constexpr int kSpinLimit = 1 << 22;  // default look-back polls before giving up (error flag)
+
+// Rounds of look-back reads a sort tile may make (DevScalars::spin_limit: 0
+// the default, > 0 that many, < 0 none: the first round gives up).
+__device__ __forceinline__ int spin_limit_of(const DevScalars *sc)
+{
+    const int v = sc->spin_limit;
+    return v == 0 ? kSpinLimit : (v < 0 ? 0 : v);
+}
+
 
 // Space-filling-curve key of every particle (star id above the 3*bits bits of
 // the cell's Hilbert index), its identity value, and the digit histograms of
@@ -281,8 +286,10 @@ constexpr int kLookback = 8;  // predecessor words read together per look-back s
 // Look-back reads kLookback lower tiles per step, so a tile whose
 // predecessors have only published counts still finds its prefix in a few
 // steps instead of waiting for a chain of prefixes.
-// A poll that never sees a lower tile's word gives up after kSpinLimit
-// tries and raises ERR_TIMEOUT (the sort is then invalid, the host reports it).
+// A tile that has made spin_limit_of(sc) rounds of look-back reads without
+// finding its prefix, or that sees another tile's timeout, gives up and
+// raises ERR_TIMEOUT (the sort is then invalid, the host reports it); scatter
+// indices stay in bounds.  Passes after a timed-out one return at entry.
 __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
                            unsigned long long *kout, uint32_t *vout, int64_t n, int ipt,
                            int shift, const uint32_t *digit_total, unsigned long long *status,
@@ -294,6 +301,8 @@ __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
     __shared__ uint32_t wc[kSortThreads / 32][256];
     __shared__ int s_tile;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (order_invalid(sc)) return;  // uniform: set by an earlier pass
+    const int limit = spin_limit_of(sc);
     if (t == 0) s_tile = (int)atomicAdd(tile_next, 1u);
     cnt[t] = 0u;
     // base of digit t: keys of this pass with a smaller digit
@@ -324,6 +333,12 @@ __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
         int k = tile - 1;
         int polls = 0;
         while (k >= 0) {
+            // a bounded wait: give up after `limit` rounds of reads, or at
+            // once when another tile has already given up
+            if (polls++ >= limit || order_invalid(sc)) {
+                atomicOr(&sc->err, ERR_TIMEOUT);
+                break;
+            }
             // read up to kLookback lower tiles at once, then add them in order
             // until a prefix (done) or a word not yet written (poll again)
             unsigned long long w[kLookback];
@@ -346,10 +361,6 @@ __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
             }
             k -= used;
             if (done) break;
-            if (stall && ++polls > kSpinLimit) {
-                atomicOr(&sc->err, ERR_TIMEOUT);
-                break;
-            }
         }
         st_relaxed_u64(mine, (2ull << 32) | (excl + c));
     }
@@ -390,23 +401,6 @@ __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
     }
 }
 
-// A float as a double, by moving its exponent and mantissa bits (exact for
-// zero and normal floats; subnormals take the conversion instruction).
-__device__ __forceinline__ double float_to_double_exact(float f)
-{
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t ex = (b >> 23) & 0xffu, man = b & 0x7fffffu;
-    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
-    if (ex == 0u) {
-        if (man == 0u) return __longlong_as_double((long long)sign);
-        return (double)f;
-    }
-    if (ex == 0xffu) return (double)f;
-    const unsigned long long bits =
-        sign | ((unsigned long long)(ex - 127u + 1023u) << 52) | ((unsigned long long)man << 29);
-    return __longlong_as_double((long long)bits);
-}
-
 // Sorted copies and the FP32 j-record halves read by the list build.  order
 // may be perm itself (keeping the last sort's order): each thread reads and
 // rewrites only its own slot.
@@ -415,7 +409,7 @@ __global__ void k_gather(DevState st, const uint32_t *order, DevScalars *sc, int
                          float4 *rec, float4 *pos4, double4_32a *rec64)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= st.n) return;
+    if (i >= st.n || order_invalid(sc)) return;
     uint32_t o = order[i];
     if ((int64_t)o >= st.n) {  // only after a failed sort (its error flag is set too)
         atomicOr(&sc->err, ERR_BOUNDS);
@@ -472,6 +466,7 @@ __global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int3
                        TreeLevels tl, float4 *nodes, DevScalars *sc)
 {
     __shared__ float4 sa[kTreeBlock], sb[kTreeBlock];
+    if (order_invalid(sc)) return;  // uniform across the grid
     const int t = threadIdx.x;
     const int l = blockIdx.x * kTreeBlock + t;
     const int nleaves = tl.count[0];
@@ -562,255 +557,13 @@ __global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int3
     if (t == 0) sc->tree_done = 0;
 }
 
-// Exact FP64 predicate in the oracle's operation order (no contraction).
-__device__ __forceinline__ bool pair_in_fp64(double xa, double ya, double za, double ha,
-                                             double xb, double yb, double zb, double hb)
-{
-    double dx = __dsub_rn(xa, xb), dy = __dsub_rn(ya, yb), dz = __dsub_rn(za, zb);
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    double hsum = __dadd_rn(ha, hb);
-    return r2 < __dmul_rn(hsum, hsum);
-}
-
-constexpr int kListThreads = 64;
-constexpr int kListWarps = kListThreads / 32;
-constexpr int kGroup = 8;                              // particles per warp
-constexpr int kSub = 32 / kGroup;                      // lanes per particle
-constexpr int kChildRounds = kBranch / kSub;           // child tests per lane and node
-constexpr int kLeafRounds = kLeaf / kSub;              // pair tests per lane and leaf
-static_assert(kGroup * kSub == 32 && kGroup <= 16 && kChildRounds >= 1 && kLeafRounds >= 1,
-              "group shape");
-// bit kGroup*s set for s = 0 .. kSub-1: picks one particle's bits out of a ballot
-constexpr unsigned spread_bits()
-{
-    unsigned m = 0;
-    for (int s = 0; s < kSub; ++s) m |= 1u << (kGroup * s);
-    return m;
-}
-constexpr unsigned kSpread = spread_bits();
-constexpr int kCandCap = 256;                          // candidate leaves buffered per warp
-constexpr int kStackCap = (kBranch - 1) * 10 + 2;      // depth bound for <= 10 levels
-
-// One warp per 8 consecutive sorted particles, four lanes per particle:
-// lane = 8 s + q serves particle q as its sub-lane s.
-//
-// Phase 1 walks the implicit 8-ary tree depth first with a warp-uniform
-// stack in shared memory.  The 8 children of a popped node are tested in two
-// rounds, sub-lane s taking child 4r + s against its particle (box distance
-// below h_q + h_max(child)); the two ballots give every child an 8-bit mask
-// of the particles it may hold neighbours of.  Children hit by some particle
-// are pushed in reverse order (inner nodes) or appended with their mask to a
-// shared leaf buffer (leaves), so the buffer stays in ascending leaf order.
-// Phase 2: the four sub-lanes of particle q step together through the
-// buffered leaves whose mask has bit q; sub-lane s screens the leaf's
-// particles s and s + 4.  Two ballots give the particle's 8-bit hit mask, so
-// each hit is written at its rank: lists are in ascending sorted index.
-//
-// Screening uses FP32 positions (pos4 = fl32(x, y, z, h)).  With u = 2^-24
-// and X = max |x|, |fl32 error of r^2 - (h_a+h_b)^2| <= 4 sqrt(3) u X r +
-// 5 u r^2 + 7 u hs^2 for r <= 2 hs; the band M = c1 hs + 3.2e-6 hs^2 with
-// c1 = 1.67e-6 X is twice that bound.  Inside the band the pair is decided
-// by the FP64 predicate.
-// At most 64 registers (16 blocks of 2 warps per SM): the walk is latency
-// bound and gains more from resident warps than from extra registers.
-template <bool MULTI_STAR>
-__global__ void __launch_bounds__(kListThreads, 16)
-k_neighbors(int64_t n, const float4 *pos4, const double *xs, const double *ys, const double *zs,
-            const double *hs, const int32_t *leaf_start, const int32_t *leaf_star,
-            const int32_t *leaf_of, TreeLevels tl, const float4 *nodes, int cap, int32_t *nbr,
-            int32_t *ncnt, DevScalars *sc)
-{
-    __shared__ int2 s_leaf[kListWarps][kCandCap];    // particle range of a buffered leaf
-    __shared__ unsigned short s_mask[kListWarps][kCandCap];
-    __shared__ unsigned s_stack[kListWarps][kStackCap];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = lane & (kGroup - 1), sub = lane / kGroup;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const float c1 = sc->screen_c1;
-    const float eps = (float)sc->eps_abs;
-    const int64_t ngroups = (n + kGroup - 1) / kGroup;
-    unsigned *stack = s_stack[warp];
-    unsigned long long nre = 0, pairs = 0;
-    bool over = false;
-    // Persistent warps: each claims the next group of sorted particles from a
-    // counter (reset at the start of every right-hand side), which evens out
-    // the uneven cost of groups across the SMs.
-    while (true) {
-    int64_t grp = 0;
-    if (lane == 0) grp = (int64_t)atomicAdd(&sc->list_next, 1u);
-    grp = __shfl_sync(0xffffffffu, grp, 0);
-    if (grp >= ngroups) break;
-    const int64_t i = grp * kGroup + q;
-    const bool valid = i < n;
-    int cnt = 0;  // equal on the four sub-lanes of a particle
-    // invalid lanes sit far away: every box and pair test fails for them
-    float4 p = make_float4(3e38f, 3e38f, 3e38f, 0.f);
-    int star = 0;
-    if (valid) {
-        p = pos4[i];
-        if (MULTI_STAR) star = leaf_star[leaf_of[i]];
-    }
-    int32_t *out = nbr + i * (int64_t)cap;
-
-    auto box_hit = [&](const float4 &a, const float4 &b) -> bool {
-        float gx = fmaxf(fmaxf(a.x - p.x, p.x - b.x), 0.f);
-        float gy = fmaxf(fmaxf(a.y - p.y, p.y - b.y), 0.f);
-        float gz = fmaxf(fmaxf(a.z - p.z, p.z - b.z), 0.f);
-        float R = fmaf(p.w + a.w, 1.0001f, eps);
-        bool h = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
-        if (MULTI_STAR) {
-            int sr = __float_as_int(b.w);
-            h = h && star >= (sr & 0xffff) && star <= (int)((unsigned)sr >> 16);
-        }
-        return h;
-    };
-    // FP32 screen with the FP64 decision inside the error band
-    auto pair_in = [&](int j) -> bool {
-        float4 o = pos4[j];
-        float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float hsum = p.w + o.w;
-        float hs2 = hsum * hsum;
-        float d = r2 - hs2;
-        float M = fmaf(c1, hsum, 3.2e-6f * hs2);
-        bool in = d < -M;
-        if (fabsf(d) <= M) {
-            ++nre;
-            in = pair_in_fp64(xs[i], ys[i], zs[i], hs[i], xs[j], ys[j], zs[j], hs[j]);
-        }
-        return in;
-    };
-
-    int sp = 0;
-    int ncand = 0;
-    const int top = tl.nlevels - 1;
-    if (top == 0) {
-        int64_t gi = tl.offset[0];
-        unsigned m = __ballot_sync(0xffffffffu, sub == 0 && box_hit(nodes[2 * gi], nodes[2 * gi + 1]));
-        if (m) {
-            if (lane == 0) {
-                s_leaf[warp][0] = make_int2(leaf_start[0], leaf_start[1]);
-                s_mask[warp][0] = (unsigned short)(m & ((1u << kGroup) - 1u));
-            }
-            ncand = 1;
-        }
-    } else {
-        if (lane == 0) stack[0] = ((unsigned)top << 26) | 0u;
-        sp = 1;
-    }
-    __syncwarp();
-    while (true) {
-        while (sp > 0 && ncand <= kCandCap - kBranch) {
-            unsigned e = stack[sp - 1];
-            --sp;
-            __syncwarp();
-            int lv = (int)(e >> 26), k = (int)(e & ((1u << 26) - 1u));
-            int c0 = kBranch * k;
-            int nc = min(kBranch, tl.count[lv - 1] - c0);
-            int64_t base = (int64_t)tl.offset[lv - 1] + c0;
-            unsigned bal[kChildRounds];
-#pragma unroll
-            for (int r = 0; r < kChildRounds; ++r) {
-                int c = kSub * r + sub;
-                bool hit = false;
-                if (c < nc) hit = box_hit(nodes[2 * (base + c)], nodes[2 * (base + c) + 1]);
-                bal[r] = __ballot_sync(0xffffffffu, hit);
-            }
-            // lane c < 8: particle mask of child c
-            const int c = lane & (kBranch - 1);
-            unsigned bc = bal[0];
-#pragma unroll
-            for (int r = 1; r < kChildRounds; ++r)
-                if (c / kSub == r) bc = bal[r];
-            unsigned cm = (bc >> (kGroup * (c % kSub))) & ((1u << kGroup) - 1u);
-            bool mine = lane < kBranch && cm != 0u;
-            unsigned any = __ballot_sync(0xffffffffu, mine);
-            int nh = __popc(any), rank = __popc(any & lt_mask);
-            if (lv == 1) {
-                if (mine) {
-                    if (MULTI_STAR) {
-                        s_leaf[warp][ncand + rank] =
-                            make_int2(leaf_start[c0 + c], leaf_start[c0 + c + 1]);
-                    } else {  // one star: leaf l holds sorted slots [8l, min(8l + 8, n))
-                        const int lo = kLeaf * (c0 + c);
-                        s_leaf[warp][ncand + rank] =
-                            make_int2(lo, (int)min((int64_t)lo + kLeaf, n));
-                    }
-                    s_mask[warp][ncand + rank] = (unsigned short)cm;
-                }
-                ncand += nh;
-            } else {
-                if (mine) stack[sp + nh - 1 - rank] = ((unsigned)(lv - 1) << 26) | (unsigned)(c0 + c);
-                sp += nh;
-            }
-            __syncwarp();
-        }
-        int cpos = 0;
-        while (true) {
-            while (cpos < ncand && !((s_mask[warp][cpos] >> q) & 1u)) ++cpos;
-            bool have = cpos < ncand;
-            if (!__any_sync(0xffffffffu, have)) break;
-            bool in[kLeafRounds];
-            int js = 0;
-            if (have) {
-                const int2 lr = s_leaf[warp][cpos];
-                ++cpos;
-                js = lr.x;
-                const int je = lr.y;
-#pragma unroll
-                for (int u = 0; u < kLeafRounds; ++u) {
-                    int j = js + kSub * u + sub;
-                    in[u] = j < je && j != (int)i && pair_in(j);
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < kLeafRounds; ++u) in[u] = false;
-            }
-            // a hit of leaf particle t = kSub u + sub goes after the particle's
-            // hits of earlier rounds and of lower sub-lanes in this round
-            int pre = cnt;
-#pragma unroll
-            for (int u = 0; u < kLeafRounds; ++u) {
-                const unsigned b = (__ballot_sync(0xffffffffu, in[u]) >> q) & kSpread;
-                if (in[u]) {
-                    int pos = pre + __popc(b & ((1u << (kGroup * sub)) - 1u));
-                    if (pos < cap) out[pos] = js + kSub * u + sub;
-                    else over = true;
-                }
-                pre += __popc(b);
-            }
-            cnt = pre;
-        }
-        __syncwarp();
-        ncand = 0;
-        if (sp == 0) break;
-    }
-    if (valid && sub == 0) ncnt[i] = cnt < cap ? cnt : cap;
-    if (sub == 0) pairs += (unsigned long long)(cnt < cap ? cnt : cap);
-    }  // group loop
-    // counters: one atomic per warp
-    unsigned long long c = pairs;
-    for (int o = 16; o > 0; o >>= 1) {
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        nre += __shfl_xor_sync(0xffffffffu, nre, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&sc->pairs_last, c);
-        atomicAdd(&sc->pairs_total, c);
-        if (nre) atomicAdd(&sc->rechecks, nre);
-    }
-    if (over) atomicOr(&sc->err, ERR_CAPACITY);
-}
-
 }  // namespace
 
-// Host-side launch sequence of the neighbour search.
+// Host-side launch sequence of the sort and the tree.
 void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
-                  const TreeLevels &tl, int nleaves, int cap, int fp64_records,
-                  cudaStream_t stream, int *nlaunch, cudaEvent_t ev_lists, int ev_external,
-                  bool resort)
+                  const TreeLevels &tl, int nleaves, int fp64_records, cudaStream_t stream,
+                  int *nlaunch, bool resort)
 {
-    const bool multi_star = plan.star_bits > 0;
     const int64_t n = st.n;
     int nl = 0;
     int64_t nb = (n + kBoxThreads - 1) / kBoxThreads;
@@ -848,32 +601,6 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     ++nl;
     k_tree<<<(nleaves + kTreeBlock - 1) / kTreeBlock, kTreeBlock, 0, stream>>>(
         s.pos4, s.leaf_start, s.leaf_star, tl, s.nodes, s.sc);
-    ++nl;
-    if (ev_lists) {
-        if (ev_external) cudaEventRecordWithFlags(ev_lists, stream, cudaEventRecordExternal);
-        else cudaEventRecord(ev_lists, stream);
-    }
-    // persistent grid: enough warps to fill every SM, never more than groups
-    static int sms = 0, per_sm_t = 0, per_sm_f = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_neighbors<true>, kListThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_neighbors<false>, kListThreads, 0);
-        if (sms < 1) sms = 1;
-    }
-    const int64_t need = (n + kGroup * kListWarps - 1) / (kGroup * kListWarps);
-    int64_t cap_blocks = (int64_t)sms * ((multi_star ? per_sm_t : per_sm_f) > 0 ? (multi_star ? per_sm_t : per_sm_f) : 1);
-    const int lb = (int)(need < cap_blocks ? need : cap_blocks);
-    if (multi_star)
-        k_neighbors<true><<<lb, kListThreads, 0, stream>>>(n, s.pos4, s.xs, s.ys, s.zs, s.hs,
-                                                           s.leaf_start, s.leaf_star, s.leaf_of,
-                                                           tl, s.nodes, cap, s.nbr, s.ncnt, s.sc);
-    else
-        k_neighbors<false><<<lb, kListThreads, 0, stream>>>(n, s.pos4, s.xs, s.ys, s.zs, s.hs,
-                                                            s.leaf_start, s.leaf_star, s.leaf_of,
-                                                            tl, s.nodes, cap, s.nbr, s.ncnt, s.sc);
     ++nl;
     if (nlaunch) *nlaunch += nl;
 }

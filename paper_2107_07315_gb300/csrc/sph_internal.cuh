@@ -17,13 +17,13 @@
 //                  (xz,yz,0,0); sd264[n][8] doubles.
 //   pp / pp64    : per-particle EoS values for the finalize step:
 //                  (rho, P, dP/drho, h_enth), (W~, c_s, D, 0).
-//   nbr[n*cap]   : neighbour list of each sorted particle (sorted indices,
-//                  ascending), ncnt[n] its length.
-//   pos4[n]      : float4 fl32(x, y, z, h) per sorted particle, read by the
-//                  FP32 screening of the list build.
+//   pos4[n]      : float4 fl32(x, y, z, h) per sorted particle (leaf boxes).
 //   tree nodes   : implicit 8-ary tree over leaves of 8 consecutive sorted
 //                  particles of one star; node = float4 (lo.xyz, h_max) +
 //                  float4 (hi.xyz, star range packed in the float bits).
+//   nbr[n*cap]   : neighbour list of each sorted particle (sorted indices,
+//                  ascending), ncnt[n] its length; written by the pair-tile
+//                  search from the 64-bit neighbour masks of its tiles.
 #pragma once
 
 #include <cstdint>
@@ -38,6 +38,8 @@ constexpr int kBranch = 8;        // children per tree node
 constexpr int kMaxLevels = 16;
 constexpr int kTreeBlock = 64;    // leaves per block in the tree kernel (8^2)
 constexpr int kTreeBlockLevels = 2;
+constexpr int kCandCap = 512;     // candidate leaves per leaf (pair tiles per leaf)
+constexpr int kRowCap = 256;      // most neighbours per particle (list capacity limit)
 
 // Device error word bits.
 enum : int {
@@ -57,15 +59,19 @@ struct DevScalars {
     float key_lo_f[3], key_scale_f[3];  // FP32 copies of the box corner and 1/extent
     float grid_f, grid_inv_f;        // FP32 copies of grid and 1/grid (powers of two)
     double eps_abs;                  // absolute slack for tree pruning
-    float screen_c1;                 // FP32 screening band coefficient (1.67e-6 max|x|)
+    float eps_abs_f;                 // FP32 copy
+    float band_abs;                  // absolute part of the FP32 screening band (48 grid 2^-24)
     int err;                         // ERR_* bits
     int tree_done;                   // block counter of the tree kernel
-    unsigned int list_next;          // next particle group of the neighbour kernel
+    int max_cand;                    // most candidate leaves of one leaf (last right-hand side)
+    int max_count;                   // most neighbours of one particle (last right-hand side)
     unsigned int tile_next[8];       // next sort tile of each radix pass
+    int spin_limit;                  // polls of a look-back wait before it gives up
     unsigned long long pairs_last;   // ordered pairs of the last RHS
     unsigned long long pairs_total;
     unsigned long long rechecks;     // marginal FP64 predicate evaluations
     unsigned long long rhs_count;
+    unsigned long long tiles_last;   // candidate (leaf, leaf) tiles of the last RHS
 };
 
 struct DevState {
@@ -86,6 +92,8 @@ struct DevEos {
     const double *K, *Gamma;
     int npieces;
     const double *rho_b, *Kp, *Gp, *ap;
+    // FP32 copies for the mixed-precision kernels
+    const float *Kf, *Gf, *rho_bf, *Kpf, *Gpf, *apf;
 };
 
 // The piece of star s's EoS that holds density rho: K, Gamma and a.
@@ -110,6 +118,16 @@ __device__ __forceinline__ void eos_piece(const DevEos &e, int s, T rho, T &K, T
 struct DevMaterial {
     double alpha_av, beta_av, eta2;
     int jaumann, yield_mode, break_stress, break_zero_S;
+    float alpha_f, beta_f, eta2_f;  // FP32 copies
+};
+
+// FP32 per-star constants of the background and the external field
+// (DevMetric::fstar, kFStar floats per star): table radius and mass, the
+// centre split into hi + lo floats, the external table radius, wall radius
+// and centre.
+enum {
+    FS_RMAX = 0, FS_M = 1, FS_CHI = 2, FS_CLO = 5, FS_EXT_RMAX = 8, FS_EXT_RWALL = 9,
+    FS_EXT_CHI = 10, FS_EXT_CLO = 13, kFStar = 16
 };
 
 // Background fields of the right-hand side: the fixed metric (Sec. I.C) and
@@ -126,6 +144,8 @@ struct DevMetric {
     const double *ext_g;  // [nstars][ext_nr]
     const float *ext_gf;  // FP32 copy
     double k_wall, damping;
+    float k_wall_f, damping_f;
+    const float *fstar;   // [nstars][kFStar] FP32 per-star constants
 };
 
 struct DevRates {
@@ -200,24 +220,32 @@ struct SortPlan {
 
 constexpr int kBoxBlocksMax = 304;
 
-// ev_lists (optional) is recorded between the tree and the neighbour-list
-// kernels; ev_external marks a record inside a stream capture.  resort false
-// keeps the particle order of s.perm (the last sort) instead of sorting
-// along the curve again: the sorted copies, the tree and the lists are still
-// rebuilt from the current positions, so the lists are the same sets.
+// Bounding box, curve keys and sort, sorted gather and leaf tree.  resort
+// false keeps the particle order of s.perm (the last sort) instead of sorting
+// along the curve again: the sorted copies and the tree are still rebuilt
+// from the current positions and h.
 void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
-                  const TreeLevels &tl, int nleaves, int cap, int fp64_records,
-                  cudaStream_t stream, int *nlaunch, cudaEvent_t ev_lists = nullptr,
-                  int ev_external = 0, bool resort = true);
+                  const TreeLevels &tl, int nleaves, int fp64_records, cudaStream_t stream,
+                  int *nlaunch, bool resort = true);
 
-void launch_density(const DevState &st, const Scratch &s, const DevEos &eos,
-                    const DevMetric &g, const DevRates &out, int cap, int lanes, int fp64,
-                    cudaStream_t stream);
+// Pair tiles (sph_tiles.cu): per leaf, the candidate leaves (tree walk) and
+// the exact neighbour lists and counts from the tiles' neighbour masks, and
+// with density true (mixed precision) the density summation and the equation
+// of state.  cap: list capacity per particle (SPH_ERR_CAPACITY above it).
+void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
+                  int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
+                  const DevRates &out, cudaStream_t stream);
 
-// Mixed precision runs an all-fluid-block kernel and a solid-block kernel
-// over the same grid; with side, fork and join given, the solid-block kernel
-// runs on side (after fork is recorded on stream) so the two overlap, and
-// stream waits on join before it goes on.
+// FP64 density summation and equation of state over the neighbour lists.
+void launch_density_fp64(const DevState &st, const Scratch &s, const DevEos &eos,
+                         const DevMetric &g, const DevRates &out, int cap, int lanes,
+                         cudaStream_t stream);
+
+// Force pass over the neighbour lists.  Mixed precision runs an
+// all-fluid-block kernel and a solid-block kernel over the same grid; with
+// side, fork and join given, the solid-block kernel runs on side (after fork
+// is recorded on stream) so the two overlap, and stream waits on join before
+// it goes on.
 void launch_force(const DevState &st, const Scratch &s, const DevEos &eos,
                   const DevMaterial &mat, const DevMetric &g, const DevRates &out, int cap,
                   int lanes, int fp64, cudaStream_t stream, cudaStream_t side = nullptr,
@@ -248,6 +276,8 @@ void launch_totals(const StepState &s, const int32_t *ncount, double *partial, d
                    cudaStream_t st);
 void launch_export_counts(const Scratch &s, int64_t n, int64_t *counts_out,
                           cudaStream_t st);
+// Neighbour lists of the last right-hand side in caller order and ascending
+// caller index (offsets from the counts by an exclusive scan).
 void launch_export_fill(const Scratch &s, int64_t n, int cap, const int64_t *offsets,
                         int32_t *idx, cudaStream_t st);
 void launch_scan_i64(int64_t *data, int64_t n, cudaStream_t st);

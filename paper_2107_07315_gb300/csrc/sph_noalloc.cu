@@ -6,17 +6,20 @@
 // or time-critical loops where an allocator call (which may synchronise the
 // device) is not allowed.  This entry point computes the same CSR neighbour
 // lists as sph_neighbors without a context and without allocating: its
-// scratch is one fixed file-scope device array.  Its first call on a device
-// looks up the array's device address with that device current; make that
-// first call before any stream capture.
+// scratch is one fixed file-scope device array.  Every call looks up the
+// array's device address on the current device (the lookup allocates
+// nothing), so a context that was reset or re-created is never handed a stale
+// address.
 //
 // Limits: at most kMaxN particles of one star, at most kCap neighbours per
-// particle.  The array (about 11.7 MB) exists on every GPU that loads this
-// library and stays there until the process exits.  All calls share it:
-// calls that overlap on the GPU (different streams or threads without
+// particle and kCandCap candidate leaves (groups of 8 sorted particles) per
+// leaf.  The array (about 11.7 MB) exists on every GPU that loads this library
+// and stays there until the process exits.  With lazy module loading (the
+// CUDA default) the first call on a device loads this library's device code
+// and the array, which takes device memory once: make one call with n >= 1
+// before another allocator takes the whole device.  All calls share the
+// array: calls that overlap on the GPU (different streams or threads without
 // ordering between them) race on it.
-#include <mutex>
-
 #include "sph_internal.cuh"
 
 namespace {
@@ -62,30 +65,24 @@ constexpr size_t kBytes = kPos4 + align256(kMaxN * 16);
 
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
-// Per-device address of g_scratch, looked up once with that device current.
-std::mutex g_mu;
-void *g_addr[64] = {};
-
 sph_status fail(sph_status s, const char *m)
 {
     record_error(m);  // readable through sph_last_error()
     return s;
 }
 
-sph_status scratch_for_current_device(unsigned char **out)
+// Device address of g_scratch on the current device.  In host code the
+// array's name is only a stand-in; the runtime gives the address the device
+// uses, looked up anew on every call.
+sph_status scratch_address(unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-        return fail(SPH_ERR_NODEVICE, "sph_neighbors_noalloc: no current CUDA device");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: cudaGetSymbolAddress failed");
-        g_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: cudaGetSymbolAddress failed");
     }
-    *out = (unsigned char *)g_addr[dev];
+    *out = (unsigned char *)p;
     return SPH_OK;
 }
 
@@ -122,13 +119,23 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
         cudaGetLastError();
         return fail(SPH_ERR_NODEVICE, "sph_neighbors_noalloc: no CUDA device");
     }
+    // an error left pending by earlier, unrelated runtime calls is not ours
+    cudaGetLastError();
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     unsigned char *base = nullptr;
-    sph_status st0 = scratch_for_current_device(&base);
+    sph_status st0 = scratch_address(&base);
     if (st0 != SPH_OK) return st0;
-    if (cudaMemsetAsync(offsets, 0, (size_t)(n + 1) * sizeof(int64_t), stream) != cudaSuccess)
+    if (cudaMemsetAsync(offsets, 0, (size_t)(n + 1) * sizeof(int64_t), stream) != cudaSuccess) {
+        cudaGetLastError();
         return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: memset of offsets failed");
-    if (n == 0) return cudaStreamSynchronize(stream) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+    }
+    if (n == 0) {
+        if (cudaStreamSynchronize(stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: stream synchronisation failed");
+        }
+        return SPH_OK;
+    }
 
     Scratch s{};
     s.perm = (int32_t *)(base + kPerm);
@@ -168,12 +175,16 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
     TreeLevels tl{};
     make_tree_levels(nleaves, tl, nullptr);
 
-    // Scratch state that must start at zero on every call.
+    // Scratch state that must start at zero on every call (the DevScalars
+    // block holds the error word, the counters and the default wait limit).
     bool ok = cudaMemsetAsync(s.bbox_done, 0, sizeof(unsigned int), stream) == cudaSuccess &&
               cudaMemsetAsync(s.sc, 0, sizeof(DevScalars), stream) == cudaSuccess &&
               cudaMemsetAsync(mass, 0, (size_t)n * sizeof(double), stream) == cudaSuccess &&
               cudaMemsetAsync(type, 0, (size_t)n, stream) == cudaSuccess;
-    if (!ok) return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: scratch reset failed");
+    if (!ok) {
+        cudaGetLastError();
+        return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: scratch reset failed");
+    }
     k_leaf_layout<<<(int)((n + 256) / 256), 256, 0, stream>>>(n, nleaves, s.leaf_start,
                                                                s.leaf_star, s.leaf_of);
     DevState st{};
@@ -188,24 +199,39 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
     st.mu = nullptr;
     st.type = type;
     st.star = nullptr;
-    launch_build(st, s, plan, tl, nleaves, kCap, 0, stream, nullptr);
+    launch_build(st, s, plan, tl, nleaves, 0, stream, nullptr);
+    // the tile kernel without the density pass reads no rate or EoS field
+    launch_tiles(st, s, tl, nleaves, 0, kCap, 0, DevEos{}, DevMetric{}, DevRates{}, stream);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: a neighbour-search launch failed");
     launch_export_counts(s, n, offsets, stream);
     launch_scan_i64(offsets, n + 1, stream);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: the count or scan launch failed");
     int64_t tot = 0;
     int err = 0;
     if (cudaMemcpyAsync(&tot, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(&err, &s.sc->err, sizeof(int), cudaMemcpyDeviceToHost, stream) !=
             cudaSuccess ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
         return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: kernel or copy failed");
+    }
     if (err & ERR_NONFINITE) return fail(SPH_ERR_NONFINITE, "sph_neighbors_noalloc: non-finite x or h");
     if (err & ERR_TIMEOUT) return fail(SPH_ERR_TIMEOUT, "sph_neighbors_noalloc: sort wait timed out");
     if (err & ERR_CAPACITY)
-        return fail(SPH_ERR_CAPACITY, "sph_neighbors_noalloc: a particle has more than 128 neighbours");
+        return fail(SPH_ERR_CAPACITY,
+                    "sph_neighbors_noalloc: a particle has more than 128 neighbours, or a leaf "
+                    "more than 512 candidate leaves");
+    if (err & ERR_BOUNDS) return fail(SPH_ERR_BOUNDS, "sph_neighbors_noalloc: index out of bounds");
     if (tot > cap) return fail(SPH_ERR_CAPACITY, "sph_neighbors_noalloc: lists exceed cap");
     launch_export_fill(s, n, kCap, offsets, idx, stream);
-    if (cudaStreamSynchronize(stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: the export launch failed");
+    if (cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
         return fail(SPH_ERR_CUDA, "sph_neighbors_noalloc: export failed");
+    }
     return SPH_OK;
 }

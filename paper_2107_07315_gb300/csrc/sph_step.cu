@@ -256,6 +256,8 @@ __global__ void k_scan_i64(int64_t *data, int64_t n)
     }
 }
 
+// Row of sorted particle i in caller order: its list as caller indices in
+// ascending order (insertion sort).
 __global__ void k_export_fill(const int32_t *perm, const int32_t *nbr, const int32_t *ncnt,
                               int64_t n, int cap, const int64_t *offsets, int32_t *idx)
 {

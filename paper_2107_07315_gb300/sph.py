@@ -27,7 +27,7 @@ STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
 EXPORTS = ("sph_init", "sph_rhs", "sph_step", "sph_sync", "sph_neighbors", "sph_totals",
            "sph_stats", "sph_timing", "sph_timing_read", "sph_state_size", "sph_get_state",
            "sph_set_state", "sph_free", "sph_last_error", "sph_neighbors_noalloc",
-           "sph_set_external", "sph_relax_finish")
+           "sph_set_external", "sph_relax_finish", "sph_set_wait_limit")
 
 
 class SphError(RuntimeError):
@@ -113,6 +113,7 @@ def lib():
         L.sph_rhs.argtypes = [vp, C.POINTER(sph_rates)]
         L.sph_step.argtypes = [vp, C.c_double, C.c_int32]
         L.sph_sync.argtypes = [vp]
+        L.sph_set_wait_limit.argtypes = [vp, C.c_int32]
         L.sph_neighbors.argtypes = [vp, vp, vp, C.c_int64]
         L.sph_totals.argtypes = [vp, _d]
         L.sph_stats.argtypes = [vp, _i64]
@@ -333,6 +334,10 @@ def sph_sync(ctx: SphCtx) -> None:
     _check(lib().sph_sync(ctx.handle), "sph_sync")
 
 
+def sph_set_wait_limit(ctx: SphCtx, polls: int) -> None:
+    _check(lib().sph_set_wait_limit(ctx.handle, int(polls)), "sph_set_wait_limit")
+
+
 def sph_neighbors(ctx: SphCtx, offsets, idx, cap: int) -> None:
     _check(lib().sph_neighbors(ctx.handle, _ptr(offsets), _ptr(idx), int(cap)), "sph_neighbors")
 
@@ -344,7 +349,7 @@ def sph_totals(ctx: SphCtx) -> np.ndarray:
 
 
 def sph_stats(ctx: SphCtx) -> np.ndarray:
-    out = np.zeros(16, np.int64)
+    out = np.zeros(24, np.int64)
     _check(lib().sph_stats(ctx.handle, out.ctypes.data_as(_i64)), "sph_stats")
     return out
 
