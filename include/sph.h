@@ -148,7 +148,14 @@ typedef struct {
  * sort's order on the others; every step still rebuilds the tree and the
  * neighbour lists from the current positions, so the lists are the same
  * sets (only the order of pair sums, hence rounding, depends on k)
- * [0 or 1: every step].  sph_rhs always sorts. */
+ * [0 or 1: every step].  sph_rhs always sorts.
+ * skin: the neighbour search builds candidate lists of every pair within
+ * (1 + skin)(h_a + h_b) and screens them exactly on every right-hand side;
+ * it builds them again after a curve sort or once a particle may have moved
+ * or grown into a pair they miss (a device-side test on the largest
+ * displacement and h growth since the build), so the exact lists are the
+ * same as with lists built every time [0: 0.1; negative: build on every
+ * right-hand side; at most 1]. */
 typedef struct {
     int32_t h_nmin, h_nmax;
     int32_t max_neighbors;
@@ -156,6 +163,7 @@ typedef struct {
     int32_t use_graph;
     int32_t totals_every;
     int32_t sort_every;
+    double skin;
 } sph_options;
 
 /* Create a context bound to the particle buffers.  Validates the inputs,
@@ -216,9 +224,10 @@ sph_status sph_totals(sph_ctx *ctx, double out[16]);
  * 7 lanes per particle, 8 1 if steps run as a CUDA graph, 9 steps taken,
  * 10 radix passes, 11 cell bits per axis of the curve key, 12 kernel
  * launches issued by sph_step (cumulative), 13 steps per curve sort,
- * 14 most candidate leaves of one leaf (pair tiles), 15 most neighbours of
- * one particle, 16 candidate (leaf, leaf) tiles in all (14-16 of the last
- * right-hand side), 17 1 for mixed precision, 18-23 zero.  Synchronous. */
+ * 14 most candidate leaves of one leaf and 16 candidate (leaf, leaf) tiles
+ * in all (both of the last candidate-list build), 15 most neighbours of one
+ * particle (last right-hand side), 17 1 for mixed precision, 18 candidate-list
+ * builds so far, 19-23 zero.  Synchronous. */
 sph_status sph_stats(sph_ctx *ctx, int64_t out[24]);
 
 /* Device-time measurement with CUDA events on the context's stream.
@@ -270,7 +279,7 @@ void sph_free(sph_ctx *ctx);
  * sph_neighbors for one star: x, y, z, h are device arrays of n particles
  * (caller order), offsets a device int64[n+1], idx a device int32[cap];
  * cuda_stream a cudaStream_t (NULL: legacy default stream).  Scratch is one
- * fixed device array of about 11.7 MB inside the library, present on every
+ * fixed device array of about 11.9 MB inside the library, present on every
  * GPU that loads it until the process exits.  Limits: n <= 16384 (larger n
  * returns SPH_ERR_ARG), at most 128 neighbours per particle and 512
  * candidate leaves (groups of 8 sorted particles) per leaf

@@ -339,18 +339,19 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
     rec(c, slot_ev(c, EV_BUILD), capturing);
     launch_build(st, c->s, c->plan, c->tl, c->nleaves, fp64, c->stream, nlaunch, resort);
     rec(c, slot_ev(c, EV_LISTS), capturing);
-    // pair tiles; in mixed precision the density and equation of state too
+    // candidate lists (when stale) and exact lists; in mixed precision the
+    // density and equation of state too
     launch_tiles(st, c->s, c->tl, c->nleaves, c->multi, c->cap, fp64 ? 0 : 1, eos_of(c), c->met,
-                 out, c->stream);
+                 out, c->stream, nlaunch);
     rec(c, slot_ev(c, EV_DENSITY), capturing);
     if (fp64) launch_density_fp64(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->stream);
     rec(c, slot_ev(c, EV_FORCE), capturing);
     launch_force(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->lanes, fp64, c->stream,
                  c->side, c->ev_fork, c->ev_join);
     rec(c, slot_ev(c, EV_FORCE_END), capturing);
-    // tiles, then density and force (FP64) or the fluid-block and solid-block
-    // force kernels (mixed precision)
-    if (nlaunch) *nlaunch += 3;
+    // density and force (FP64) or the fluid-block and solid-block force
+    // kernels (mixed precision)
+    if (nlaunch) *nlaunch += 2;
 }
 
 void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch, bool resort)
@@ -529,6 +530,8 @@ sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_materi
         if (opt->h_nmax < 0 || opt->h_nmin < 0 || (opt->h_nmax > 0 && opt->h_nmin > opt->h_nmax))
             return fail(SPH_ERR_ARG, "h_nmin/h_nmax band invalid");
         if (opt->sort_every < 0) return fail(SPH_ERR_ARG, "sort_every must be >= 0");
+        if (!std::isfinite(opt->skin) || opt->skin > 1.0)
+            return fail(SPH_ERR_ARG, "skin must be finite and <= 1");
     }
     return SPH_OK;
 }
@@ -628,6 +631,9 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
         STATUS_TRY(c->alloc(&s.sd264, 8 * nn));
         STATUS_TRY(c->alloc(&s.pp64, 8 * nn));
     }
+    STATUS_TRY(c->alloc(&s.vlist, (size_t)nn * c->cap));
+    STATUS_TRY(c->alloc(&s.vcnt, nn));
+    STATUS_TRY(c->alloc(&s.pos_build, nn));
     STATUS_TRY(c->alloc(&s.nbr, (size_t)nn * c->cap));
     STATUS_TRY(c->alloc(&s.ncnt, nn));
     STATUS_TRY(c->alloc(&s.nodes, 2 * (size_t)(total_nodes > 0 ? total_nodes : 1)));
@@ -640,6 +646,15 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     CUDA_TRY(cudaMemset(s.bbox_done, 0, sizeof(unsigned int)));
     CUDA_TRY(cudaMemset(s.sc, 0, sizeof(DevScalars)));
     CUDA_TRY(cudaMemset(s.ncnt, 0, nn * sizeof(int32_t)));
+    CUDA_TRY(cudaMemset(s.vcnt, 0, nn * sizeof(int32_t)));
+    CUDA_TRY(cudaMemset(s.pos_build, 0, nn * sizeof(float4)));
+    {
+        // eps of the candidate lists: option 0 the default 0.1, < 0 none
+        // (built for every right-hand side)
+        const double o = c->opt.skin;
+        const float skin = o == 0.0 ? 0.1f : (o < 0.0 ? -1.f : (float)o);
+        CUDA_TRY(cudaMemcpy(&s.sc->skin, &skin, sizeof(float), cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(cudaMemcpy(s.leaf_start, leaf_start.data(), leaf_start.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice));
     if (!leaf_star.empty())
@@ -1012,6 +1027,7 @@ sph_status sph_stats(sph_ctx *c, int64_t out[24])
     out[15] = sc.max_count;
     out[16] = (int64_t)sc.tiles_last;
     out[17] = c->prec == SPH_FP64 ? 0 : 1;
+    out[18] = (int64_t)sc.builds;
     return SPH_OK;
 }
 

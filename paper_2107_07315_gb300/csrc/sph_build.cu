@@ -146,10 +146,12 @@ __global__ void k_bbox(DevState st, unsigned long long *partial, unsigned int *d
         // absolute part of the tile screening band: 48 g u with u = 2^-24
         sc->band_abs = (float)(48.0 * ldexp(sc->grid, -24));
         sc->pairs_last = 0ull;
-        sc->tiles_last = 0ull;
         sc->tree_done = 0;
-        sc->max_cand = 0;
         sc->max_count = 0;
+        sc->disp2_max = 0u;
+        sc->growth_max = 0u;
+        sc->resorted = 0;
+        sc->xmax_f = (float)m * 1.000001f;
         sc->rhs_count += 1ull;
         *done = 0u;
     }
@@ -218,12 +220,13 @@ __device__ __forceinline__ int spin_limit_of(const DevScalars *sc)
 // the cell's Hilbert index), its identity value, and the digit histograms of
 // all radix passes at once (a digit count does not depend on the key order).
 // Also clears the tile status words of all passes.
-__global__ void k_keys_hist(DevState st, const DevScalars *sc, int bits, int passes,
+__global__ void k_keys_hist(DevState st, DevScalars *sc, int bits, int passes,
                             unsigned long long *keys, uint32_t *vals, uint32_t *radix_tot,
                             unsigned long long *status, int64_t status_words)
 {
     __shared__ uint32_t h[kMaxPasses][256];
     for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->resorted = 1;  // the candidate lists are stale
     __syncthreads();
     // cell coordinates in FP32 (any fixed map of position to cell serves the
     // ordering; the clamp absorbs rounding at the box faces)
@@ -458,12 +461,43 @@ __device__ __forceinline__ float4 node_merge_b(float4 a, float4 b)
                        __int_as_float((int)((unsigned)lo | ((unsigned)hi << 16))));
 }
 
+// Whether the candidate lists must be built again for this right-hand side
+// (the last block of the tree kernel decides, once every block has reduced
+// the displacements and h growth since the lists were built).  A pair within
+// h_a + h_b now was within (1 + g)(h_a0 + h_b0) + 2D when the lists were built
+// (g the largest relative growth of h, D the largest displacement), so lists
+// of every pair within (1 + eps)(h_a0 + h_b0) hold every neighbour while
+// 2D <= (eps - g) 2 h_min0.  D and g come from fl32 positions and h; the
+// margins cover their rounding (u |x| per coordinate, 3u per ratio).
+__device__ void decide_rebuild(DevScalars *sc)
+{
+    const float eps = sc->skin;
+    bool rebuild = !sc->built || sc->resorted || !(eps >= 0.f);
+    if (!rebuild) {
+        const float g = fmaxf(__uint_as_float(*(volatile unsigned *)&sc->growth_max), 0.f) + 4e-7f;
+        const float D = sqrtf(__uint_as_float(*(volatile unsigned *)&sc->disp2_max)) * 1.000001f +
+                        4.f * 5.9604645e-8f * sc->xmax_f;
+        rebuild = !(g < eps) || !(2.f * D <= (eps - g) * 2.f * sc->hmin_build * 0.999999f);
+    }
+    sc->rebuild = rebuild ? 1 : 0;
+    if (rebuild) {
+        sc->built = 1;
+        sc->builds += 1ull;
+        sc->hmin_build = 3.0e38f;  // the build takes the minimum again
+        sc->tiles_last = 0ull;
+        sc->max_cand = 0;
+    }
+}
+
 // Leaf boxes and the implicit 8-ary tree above them.  Leaf boxes come from
 // pos4 = fl32(x, y, z, h) widened by one FP32 ulp outward: a round-to-nearest
 // value lies within half an ulp of the FP64 value, so the widened box holds
-// every FP64 position (and h_max bounds every FP64 h) of the leaf.
-__global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int32_t *leaf_star,
-                       TreeLevels tl, float4 *nodes, DevScalars *sc)
+// every FP64 position (and h_max bounds every FP64 h) of the leaf.  Each
+// thread also reduces its leaf's displacement and h growth since the
+// candidate lists were built (pos_build), and the last block decides whether
+// they are rebuilt.
+__global__ void k_tree(const float4 *pos4, const float4 *pos_build, const int32_t *leaf_start,
+                       const int32_t *leaf_star, TreeLevels tl, float4 *nodes, DevScalars *sc)
 {
     __shared__ float4 sa[kTreeBlock], sb[kTreeBlock];
     if (order_invalid(sc)) return;  // uniform across the grid
@@ -471,11 +505,19 @@ __global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int3
     const int l = blockIdx.x * kTreeBlock + t;
     const int nleaves = tl.count[0];
     float4 a = make_float4(3e38f, 3e38f, 3e38f, 0.f), b = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+    float d2 = 0.f, gr = 0.f;
     if (l < nleaves) {
         const int j0 = leaf_start[l], j1 = leaf_start[l + 1];
         float4 q[kLeaf];
 #pragma unroll
         for (int k = 0; k < kLeaf; ++k) q[k] = pos4[j0 + k < j1 ? j0 + k : j0];
+#pragma unroll
+        for (int k = 0; k < kLeaf; ++k) {
+            const float4 qb = pos_build[j0 + k < j1 ? j0 + k : j0];
+            const float dx = q[k].x - qb.x, dy = q[k].y - qb.y, dz = q[k].z - qb.z;
+            d2 = fmaxf(d2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            gr = fmaxf(gr, __fdiv_ru(q[k].w, qb.w) - 1.f);
+        }
         float lo[3] = {q[0].x, q[0].y, q[0].z}, hi[3] = {q[0].x, q[0].y, q[0].z}, hm = q[0].w;
 #pragma unroll
         for (int k = 1; k < kLeaf; ++k) {
@@ -529,7 +571,16 @@ __global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int3
         }
         __syncthreads();
     }
-    if (tl.nlevels - 1 <= kTreeBlockLevels) return;
+    // displacement and growth since the build: one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        gr = fmaxf(gr, __shfl_xor_sync(0xffffffffu, gr, o));
+    }
+    if ((t & 31) == 0) {
+        // NaN (lists never built) orders above every number: a rebuild
+        atomicMax(&sc->disp2_max, __float_as_uint(d2));
+        if (gr > 0.f || gr != gr) atomicMax(&sc->growth_max, __float_as_uint(gr));
+    }
     __shared__ bool last;
     if (t == 0) {
         __threadfence();
@@ -538,6 +589,7 @@ __global__ void k_tree(const float4 *pos4, const int32_t *leaf_start, const int3
     __syncthreads();
     if (!last) return;
     __threadfence();
+    if (t == 0) decide_rebuild(sc);
     for (int v = kTreeBlockLevels + 1; v < tl.nlevels; ++v) {
         for (int node = t; node < tl.count[v]; node += kTreeBlock) {
             int64_t c = (int64_t)tl.offset[v - 1] + (int64_t)kBranch * node;
@@ -600,7 +652,7 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
                                     s.pos4, fp64_records ? s.rec64 : nullptr);
     ++nl;
     k_tree<<<(nleaves + kTreeBlock - 1) / kTreeBlock, kTreeBlock, 0, stream>>>(
-        s.pos4, s.leaf_start, s.leaf_star, tl, s.nodes, s.sc);
+        s.pos4, s.pos_build, s.leaf_start, s.leaf_star, tl, s.nodes, s.sc);
     ++nl;
     if (nlaunch) *nlaunch += nl;
 }

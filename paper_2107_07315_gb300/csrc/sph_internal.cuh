@@ -21,9 +21,14 @@
 //   tree nodes   : implicit 8-ary tree over leaves of 8 consecutive sorted
 //                  particles of one star; node = float4 (lo.xyz, h_max) +
 //                  float4 (hi.xyz, star range packed in the float bits).
-//   nbr[n*cap]   : neighbour list of each sorted particle (sorted indices,
-//                  ascending), ncnt[n] its length; written by the pair-tile
-//                  search from the 64-bit neighbour masks of its tiles.
+//   vlist[n*cap] : candidate list of each sorted particle (ascending): every
+//                  b with |x_a - x_b| < (1 + eps)(h_a + h_b) when it was built
+//                  (pair-tile search), vcnt[n] its length; pos_build[n] the
+//                  fl32 positions and h it was built from.  Reused while no
+//                  particle can have moved or grown into a pair it misses.
+//   nbr[n*cap]   : exact neighbour list of each sorted particle (ascending),
+//                  ncnt[n] its length; screened from vlist every right-hand
+//                  side.
 #pragma once
 
 #include <cstdint>
@@ -38,7 +43,7 @@ constexpr int kBranch = 8;        // children per tree node
 constexpr int kMaxLevels = 16;
 constexpr int kTreeBlock = 64;    // leaves per block in the tree kernel (8^2)
 constexpr int kTreeBlockLevels = 2;
-constexpr int kCandCap = 512;     // candidate leaves per leaf (pair tiles per leaf)
+constexpr int kCandCap = 256;     // candidate leaves per leaf (pair tiles per leaf)
 constexpr int kRowCap = 256;      // most neighbours per particle (list capacity limit)
 
 // Device error word bits.
@@ -71,7 +76,18 @@ struct DevScalars {
     unsigned long long pairs_total;
     unsigned long long rechecks;     // marginal FP64 predicate evaluations
     unsigned long long rhs_count;
-    unsigned long long tiles_last;   // candidate (leaf, leaf) tiles of the last RHS
+    unsigned long long tiles_last;   // candidate (leaf, leaf) tiles of the last build
+    // candidate-list reuse (all FP32 as bit patterns of non-negative floats
+    // where noted, so atomicMax orders them)
+    float skin;                      // eps of the candidate lists (< 0: rebuild every RHS)
+    float hmin_build;                // smallest h when the lists were built
+    unsigned int disp2_max;          // largest squared displacement since the build (float bits)
+    unsigned int growth_max;         // largest h/h_build - 1 (float bits)
+    int built;                       // candidate lists exist for the current order
+    int resorted;                    // this RHS sorted along the curve again
+    int rebuild;                     // this RHS rebuilds the candidate lists
+    float xmax_f;                    // largest |coordinate| (for the displacement bound)
+    unsigned long long builds;       // candidate-list builds so far
 };
 
 struct DevState {
@@ -198,6 +214,9 @@ struct Scratch {
     double *sd264;            // [n][8]
     float4 *pp;               // [n][2]
     double *pp64;             // [n][8]
+    int32_t *vlist;           // [n][cap] (may alias nbr: then rebuilt every RHS)
+    int32_t *vcnt;            // [n]
+    float4 *pos_build;        // [n]
     int32_t *nbr;             // [n][cap]
     int32_t *ncnt;            // [n]
     float4 *nodes;            // [total nodes][2]
@@ -228,13 +247,15 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
                   const TreeLevels &tl, int nleaves, int fp64_records, cudaStream_t stream,
                   int *nlaunch, bool resort = true);
 
-// Pair tiles (sph_tiles.cu): per leaf, the candidate leaves (tree walk) and
-// the exact neighbour lists and counts from the tiles' neighbour masks, and
-// with density true (mixed precision) the density summation and the equation
-// of state.  cap: list capacity per particle (SPH_ERR_CAPACITY above it).
+// Candidate lists from pair tiles (sph_tiles.cu), when the tree kernel found
+// them stale (or always, with a negative skin): per leaf, the candidate leaves
+// (tree walk) and, per particle, every b within (1 + eps)(h_a + h_b).  Then
+// the exact lists and counts screened from the candidates, and with density
+// true (mixed precision) the density summation and the equation of state.
+// cap: list capacity per particle (SPH_ERR_CAPACITY above it).
 void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
                   int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
-                  const DevRates &out, cudaStream_t stream);
+                  const DevRates &out, cudaStream_t stream, int *nlaunch = nullptr);
 
 // FP64 density summation and equation of state over the neighbour lists.
 void launch_density_fp64(const DevState &st, const Scratch &s, const DevEos &eos,

@@ -13,7 +13,7 @@
 //
 // Limits: at most kMaxN particles of one star, at most kCap neighbours per
 // particle and kCandCap candidate leaves (groups of 8 sorted particles) per
-// leaf.  The array (about 11.7 MB) exists on every GPU that loads this library
+// leaf.  The array (about 11.9 MB) exists on every GPU that loads this library
 // and stays there until the process exits.  With lazy module loading (the
 // CUDA default) the first call on a device loads this library's device code
 // and the array, which takes device memory once: make one call with n >= 1
@@ -50,7 +50,9 @@ constexpr size_t kTys = kHs + align256(kMaxN * 8);
 constexpr size_t kRec = kTys + align256(kMaxN);
 constexpr size_t kNbr = kRec + align256(kMaxN * 4 * 16);
 constexpr size_t kNcnt = kNbr + align256((size_t)kMaxN * kCap * 4);
-constexpr size_t kNodes = kNcnt + align256(kMaxN * 4);
+constexpr size_t kVcnt = kNcnt + align256(kMaxN * 4);
+constexpr size_t kPosBuild = kVcnt + align256(kMaxN * 4);
+constexpr size_t kNodes = kPosBuild + align256(kMaxN * 16);
 constexpr size_t kLeafStart = kNodes + align256((size_t)kMaxNodes * 2 * 16);
 constexpr size_t kLeafStar = kLeafStart + align256((kMaxLeaves + 1) * 4);
 constexpr size_t kLeafOf = kLeafStar + align256(kMaxLeaves * 4);
@@ -154,6 +156,11 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
     s.pos4 = (float4 *)(base + kPos4);
     s.nbr = (int32_t *)(base + kNbr);
     s.ncnt = (int32_t *)(base + kNcnt);
+    // candidate lists are built on every call (skin 0 after the reset) and
+    // screened in place into the exact lists
+    s.vlist = s.nbr;
+    s.vcnt = (int32_t *)(base + kVcnt);
+    s.pos_build = (float4 *)(base + kPosBuild);
     s.nodes = (float4 *)(base + kNodes);
     s.leaf_start = (int32_t *)(base + kLeafStart);
     s.leaf_star = (int32_t *)(base + kLeafStar);

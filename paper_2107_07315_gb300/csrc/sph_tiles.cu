@@ -1,5 +1,6 @@
-// Neighbour search over pair tiles of leaves, with the density summation
-// fused in (mixed precision).
+// Neighbour search: candidate lists from pair tiles of leaves, and the exact
+// neighbour lists screened from them (with the density summation fused in,
+// mixed precision).
 //
 // The neighbour predicate is the one of Sec. I.B: b is a neighbour of a iff
 // b != a, both belong to the same star and |x_a - x_b| < 2 h_ab = h_a + h_b.
@@ -7,46 +8,59 @@
 //     r2 = (dx*dx + dy*dy) + dz*dz < (h_a + h_b)^2
 // bit for bit, in both precisions.
 //
-// One warp per leaf A (8 consecutive sorted particles of one star):
+// Candidate lists (k_tiles), built when the tree kernel finds the last ones
+// stale (a new curve order, or particles that may have moved or grown into a
+// pair the lists miss), one warp per leaf A (8 consecutive sorted particles):
 //   1. Walk: breadth first over the implicit 8-ary tree, level by level, one
 //      child per lane, the next 32 children's boxes loaded while the current
 //      ones are tested, so a level costs about one memory latency instead of
 //      one per node.  Inner nodes are kept when their box lies within
-//      h_max(A) + h_max(node) of A's box.  At the leaf level each candidate
-//      leaf B gets the 8-bit mask of A's particles q that lie within
-//      h_q + h_max(B) of B's box (its "reach"); B is kept when the mask is
-//      not empty.  Testing particles rather than A's box keeps the list short
-//      when A's 8 particles straddle a jump of the curve.
+//      s (h_max(A) + h_max(node)) of A's box, s = 1 + eps.  At the leaf level
+//      each candidate leaf B gets the 8-bit mask of A's particles q that lie
+//      within s (h_q + h_max(B)) of B's box (its "reach"); B is kept when the
+//      mask is not empty.  Testing particles rather than A's box keeps the
+//      list short when A's 8 particles straddle a jump of the curve.
 //   2. Tiles: the candidate leaves are staged in shared memory four at a time
-//      (32 particles: FP32 position relative to A's first particle, h and m;
-//      one coalesced load pair per lane), the next four loaded into registers
+//      (32 particles: FP32 position relative to A's first particle and h; one
+//      coalesced load pair per lane), the next four loaded into registers
 //      while the current ones are screened.  Lane 8r + b takes particle b of
 //      B against particle r of A (first half) and r + 4 (second half); a half
-//      whose particles cannot reach B is skipped.  The test is FP32 and,
-//      inside its error band, the FP64 predicate.  The two ballots are the
-//      tile's 64-bit neighbour mask (bit 8q + b); each hit is written to
-//      particle q's list at its rank, so lists come out in ascending sorted
-//      index.
-//   3. Mixed precision: the warp then sums the density over the lists it has
-//      just written (still in L1): four lanes per particle take every fourth
-//      neighbour, add m_b W(r_ab, h_ab) to a compensated (Kahan) sum and
-//      combine in a fixed order; the self term m_a W(0, h_a) is added and one
-//      lane per particle runs the equation of state (Eq. poly_eos, Sec. II.A)
-//      and rho = D/(sqrt(gamma) W) (Sec. I.C).  Summing over the lists touches
-//      only true pairs, a seventh of the screened ones.
+//      whose particles cannot reach B is skipped.  A pair is kept when its
+//      FP32 distance is below s (h_a + h_b) or within the FP32 error band of
+//      it (a superset is all a candidate list needs); missing particles sit
+//      at +-3e18 and the self pair is cleared from the self tile.  The two
+//      ballots are the tile's 64-bit mask (bit 8q + b), kept in shared
+//      memory; a decode pass then writes each particle's list: four lanes per
+//      particle take four tiles at a time, a 4-lane prefix of their counts
+//      places the entries, so lists come out in ascending sorted index.
 //
-// FP32 screening band.  Positions are Xhi + Xlo with Xhi on a grid g (a power
+// Exact lists (k_screen), every right-hand side: four lanes per particle take
+// every fourth candidate, test it in FP32 on the two-float positions and,
+// inside the error band, with the FP64 predicate; hits are written at their
+// rank (ascending) and counted.  In mixed precision the four lanes then take
+// every fourth entry of the exact list, sum m_b W(r_ab, h_ab) in a compensated
+// (Kahan) sum per lane and combine in a fixed order, so the density does not
+// depend on which candidate list held the pairs; the self term is added and
+// the equation of state (Eq. poly_eos, Sec. II.A) and rho = D/(sqrt(gamma) W)
+// (Sec. I.C) evaluated.
+//
+// FP32 screening bands.  Positions are Xhi + Xlo with Xhi on a grid g (a power
 // of two, |x|/g < 2^22), |x - Xhi| <= 3g/4 and |Xlo - fl32(x - Xhi)| <= 3gu/4
-// (u = 2^-24).  Relative to A's first particle O the FP32 coordinate of p is
+// (u = 2^-24).  On the two-float positions (k_screen) each computed component
+// dx carries at most u|dx| + 3gu of error, and r2 - (h_a + h_b)^2 computed in
+// FP32 differs from its exact value by at most 5u r2 + 5u hs^2 + 3.5 (3gu) r +
+// u|d|; the band M = 2e-6 (r2 + hs^2) + 48 g u hs is more than three times
+// that bound for r <= 2 hs (and for r > 2 hs, d > 3 hs^2 >> M).  In the tiles,
+// relative to A's first particle O the FP32 coordinate of p is
 // X_p = (Xhi_p - Xhi_O) + (Xlo_p - Xlo_O): the first difference is exact, so X_p
 // carries at most 3gu + u|x_p - x_O| of error.  For a in A (|x_a - x_O| <= e,
 // the extent of A's box) and b at separation D = x_a - x_b, each computed
 // component of X_a - X_b carries at most 6gu + 2ue + 2u|D_k|, and
 // r2 - (h_a + h_b)^2 computed in FP32 differs from its exact value by at most
-// 7u r2 + 5u hs^2 + 3.5 (6gu + 2ue) r + u|d| (hs = h_a + h_b; FP32 h carries u).
-// The band M = 2e-6 (r2 + hs^2) + 48 u (g + e) hs is more than three times that
-// bound for r <= 2 hs (and for r > 2 hs, d > 3 hs^2 >> M): outside the band the
-// FP32 sign is the exact sign, inside it the FP64 predicate decides.
+// 7u r2 + 5u hs^2 + 3.5 (6gu + 2ue) r + u|d| (hs = h_a + h_b; FP32 h carries u),
+// and the band takes 48 u (g + e) hs for its absolute part.  Outside a band
+// the FP32 sign is the exact sign; inside it the FP64 predicate decides (exact
+// lists) or the pair is kept (candidate lists).
 #include "sph_device.cuh"
 
 namespace sph {
@@ -68,10 +82,9 @@ __device__ __forceinline__ bool pair_in_fp64(double xa, double ya, double za, do
     return r2 < __dmul_rn(hsum, hsum);
 }
 
-template <bool MULTI_STAR, bool DENSITY>
+template <bool MULTI_STAR>
 __global__ void __launch_bounds__(kTileThreads, 8)
-k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos, DevMetric g,
-        DevRates out)
+k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
 {
     __shared__ int s_front[kTileWarps][2][kCandCap];
     __shared__ unsigned char s_reach[kTileWarps][2][kCandCap];
@@ -79,16 +92,18 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos,
     __shared__ float4 s_A[kTileWarps][kLeaf][2];     // A's records (Xhi, h), (Xlo, m)
     __shared__ float4 s_stage[kTileWarps][2][kChunk * kLeaf];  // (X, h) relative to A's first particle
     __shared__ int2 s_lr[kTileWarps][2][kChunk];
+    __shared__ uint2 s_mask[kTileWarps][kCandCap];   // tile masks: rows 0-3, rows 4-7
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = blockIdx.x * kTileWarps + w;
     // whole warps only (no block-wide barrier below); nothing consumes an
-    // order whose sort timed out
-    if (A >= nleaves || order_invalid(s.sc)) return;
+    // order whose sort timed out; nothing to do while the lists are valid
+    if (A >= nleaves || order_invalid(s.sc) || !s.sc->rebuild) return;
     const int64_t n = st.n;
     const unsigned lt = (1u << lane) - 1u;
     DevScalars *sc = s.sc;
     const float eps = sc->eps_abs_f;
     const float band_abs = sc->band_abs;
+    const float scale = 1.f + fmaxf(sc->skin, 0.f);  // s = 1 + eps of the candidate lists
 
     const int2 ar = leaf_range<MULTI_STAR>(s.leaf_start, A, n);
     const int na = ar.y - ar.x;
@@ -112,7 +127,7 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos,
         const float gx = fmaxf(fmaxf(lo.x - Ahi.x, Alo.x - hi.x), 0.f);
         const float gy = fmaxf(fmaxf(lo.y - Ahi.y, Alo.y - hi.y), 0.f);
         const float gz = fmaxf(fmaxf(lo.z - Ahi.z, Alo.z - hi.z), 0.f);
-        const float R = fmaf(Alo.w + lo.w, 1.0001f, eps);
+        const float R = fmaf((Alo.w + lo.w) * scale, 1.0001f, eps);
         return fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
     };
     // particles of A within h_q + h_max of a leaf box (fl32 positions; leaf
@@ -125,7 +140,7 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos,
             const float gx = fmaxf(fmaxf(lo.x - pk.x, pk.x - hi.x), 0.f);
             const float gy = fmaxf(fmaxf(lo.y - pk.y, pk.y - hi.y), 0.f);
             const float gz = fmaxf(fmaxf(lo.z - pk.z, pk.z - hi.z), 0.f);
-            const float R = fmaf(pk.w + lo.w, 1.0001f, eps);
+            const float R = fmaf((pk.w + lo.w) * scale, 1.0001f, eps);
             r |= (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R) ? (1u << k) : 0u;
         }
         return r;
@@ -211,38 +226,27 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos,
     // and hr + 4 of A
     const int hr = lane >> 3, jj = lane & 7;
     const bool v0 = hr < na, v1 = hr + 4 < na;
-    const int i0 = ar.x + hr, i1 = ar.x + hr + 4;
+    // missing rows and missing staged particles sit far apart on opposite
+    // sides: such a pair is never a hit and never inside the band
     const float4 x0 = v0 ? rel(s_A[w][hr][0], s_A[w][hr][1]) : make_float4(3e18f, 3e18f, 3e18f, 0.f);
     const float4 x1 = v1 ? rel(s_A[w][hr + 4][0], s_A[w][hr + 4][1])
                          : make_float4(3e18f, 3e18f, 3e18f, 0.f);
-    int pos0 = 0, pos1 = 0;  // list lengths of rows hr and hr + 4
-    unsigned long long nre = 0;
-    int32_t *list0 = s.nbr + (int64_t)(v0 ? i0 : ar.x) * cap;
-    int32_t *list1 = s.nbr + (int64_t)(v1 ? i1 : ar.x) * cap;
-
-    // pair test of row x (particle i) with staged particle b (j): FP32 screen,
-    // and the FP64 predicate inside the band
-    auto pair = [&](const float4 &x, const float4 &bq, bool valid, int i, int j) -> bool {
+    // candidate test of row x with staged particle b: FP32 distance below
+    // s (h_a + h_b), or within the FP32 error band of it
+    auto pair = [&](const float4 &x, const float4 &bq) -> bool {
         const float dx = x.x - bq.x, dy = x.y - bq.y, dz = x.z - bq.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float hs = x.w + bq.w;
+        const float hs = (x.w + bq.w) * scale;
         const float hs2 = hs * hs;
-        const float d = r2 - hs2;
         const float M = fmaf(kBandRel, r2 + hs2, band * hs);
-        bool in = d < -M;
-        if (valid && fabsf(d) <= M) {
-            ++nre;
-            in = pair_in_fp64(s.xs[i], s.ys[i], s.zs[i], s.hs[i], s.xs[j], s.ys[j], s.zs[j],
-                              s.hs[j]);
-        }
-        return in && valid;
+        return r2 - hs2 < M;
     };
 
     float4 nb4 = make_float4(0.f, 0.f, 0.f, 0.f);
     int2 nlr = make_int2(0, 0);
     auto load_chunk = [&](int c0) {
         const int slot = c0 + (lane >> 3), b = lane & 7;
-        nb4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        nb4 = make_float4(-3e18f, -3e18f, -3e18f, 0.f);
         if (slot < nc) {
             const int2 lr = leaf_range<MULTI_STAR>(s.leaf_start, front[slot], n);
             if (b < lr.y - lr.x) nb4 = rel(s.rec[lr.x + b], s.rec[n + lr.x + b]);
@@ -258,46 +262,164 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos,
         __syncwarp();
         if (c0 + kChunk < nc) load_chunk(c0 + kChunk);
         const int kend = min(kChunk, nc - c0);
+        uint2 mk = make_uint2(0u, 0u);  // lane k < kChunk: mask of slot c0 + k
 #pragma unroll
         for (int k = 0; k < kChunk; ++k) {
             if (k >= kend) break;  // warp-uniform
             const int2 lr = s_lr[w][buf][k];
             const unsigned reach = rfront[c0 + k];
             const float4 bq = s_stage[w][buf][k * kLeaf + jj];
-            const int j = lr.x + jj;
-            const bool vj = jj < lr.y - lr.x;
-            if (reach & 0x0fu) {
-                const bool in = pair(x0, bq, v0 && vj && j != i0, i0, j);
-                const unsigned mine = (__ballot_sync(0xffffffffu, in) >> (8 * hr)) & 0xffu;
-                if (in) {
-                    const int p = pos0 + __popc(mine & ((1u << jj) - 1u));
-                    if (p < cap) list0[p] = j;
-                }
-                pos0 += __popc(mine);
+            unsigned b0 = 0u, b1 = 0u;
+            if (reach & 0x0fu) b0 = __ballot_sync(0xffffffffu, pair(x0, bq));
+            if (reach & 0xf0u) b1 = __ballot_sync(0xffffffffu, pair(x1, bq));
+            if (lr.x == ar.x) {  // the self tile: particle q is not its own neighbour
+                b0 &= ~0x08040201u;
+                b1 &= ~0x80402010u;
             }
-            if (reach & 0xf0u) {
-                const bool in = pair(x1, bq, v1 && vj && j != i1, i1, j);
-                const unsigned mine = (__ballot_sync(0xffffffffu, in) >> (8 * hr)) & 0xffu;
-                if (in) {
-                    const int p = pos1 + __popc(mine & ((1u << jj) - 1u));
-                    if (p < cap) list1[p] = j;
-                }
-                pos1 += __popc(mine);
-            }
+            if (lane == k) mk = make_uint2(b0, b1);
+        }
+        if (lane < kend) s_mask[w][c0 + lane] = mk;
+    }
+    __syncwarp();
+
+    // decode: lane 4q + s4 takes tiles s4, s4 + 4, ... of row q; a 4-lane
+    // prefix of the hit counts places each tile's entries, so the list of
+    // row q is ascending
+    const int q = lane >> 2, s4 = lane & 3;
+    const bool vq = q < na;
+    const int64_t i = ar.x + (vq ? q : 0);
+    int32_t *lq = s.vlist + i * cap;
+    int cnt = 0;
+    for (int k0 = 0; k0 < nc; k0 += 4) {
+        const int k = k0 + s4;
+        unsigned byte = 0u;
+        int start = 0;
+        if (k < nc) {
+            const uint2 m = s_mask[w][k];
+            byte = ((q < 4 ? m.x : m.y) >> (8 * (q & 3))) & 0xffu;
+            start = leaf_range<MULTI_STAR>(s.leaf_start, front[k], n).x;
+        }
+        const int c = __popc(byte);
+        int pre = c;
+        for (int o = 1; o < 4; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, pre, o, 4);
+            if (s4 >= o) pre += y;
+        }
+        int p = cnt + pre - c;
+        cnt += __shfl_sync(0xffffffffu, pre, 3, 4);
+        while (byte) {
+            const int b = __ffs(byte) - 1;
+            byte &= byte - 1u;
+            if (p < cap) lq[p] = start + b;
+            ++p;
         }
     }
 
     // ------------------------------------------------- per-particle results
-    // row totals: rows hr and hr + 4 sit on lanes 8 hr .. 8 hr + 7
-    const int cnt0 = pos0, cnt1 = pos1;
-    if ((v0 && cnt0 > cap) || (v1 && cnt1 > cap)) over = true;
-    if (jj == 0) {
-        if (v0) s.ncnt[i0] = min(cnt0, cap);
-        if (v1) s.ncnt[i1] = min(cnt1, cap);
+    if (vq && cnt > cap) over = true;
+    if (vq && s4 == 0) {
+        s.vcnt[i] = min(cnt, cap);
+        const float4 p = s_p[w][q];
+        s.pos_build[i] = p;  // the positions and h these lists hold for
+        atomicMin((unsigned *)&sc->hmin_build, __float_as_uint(p.w));
     }
-    unsigned long long pairs = jj == 0 ? (unsigned long long)((v0 ? min(cnt0, cap) : 0) +
-                                                              (v1 ? min(cnt1, cap) : 0)) : 0ull;
-    int cmax = jj == 0 ? max(v0 ? cnt0 : 0, v1 ? cnt1 : 0) : 0;
+    if (lane == 0) {
+        atomicMax(&sc->max_cand, nc);
+        atomicAdd(&sc->tiles_last, (unsigned long long)nc);
+    }
+    if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&sc->err, ERR_CAPACITY);
+}
+
+// Exact lists from the candidate lists, every right-hand side: LPI = 4 lanes
+// per particle, 32 particles per block.  With DENSITY (mixed precision) also
+// the density summation and the equation of state.  The exact list of a
+// particle is a subsequence of its candidate list, so the two may share
+// memory: every entry is written at or before the last one read.
+constexpr int kScreenThreads = 128;
+template <bool DENSITY>
+__global__ void __launch_bounds__(kScreenThreads, 12)
+k_screen(DevState st, Scratch s, int cap, DevEos eos, DevMetric g, DevRates out)
+{
+    if (order_invalid(s.sc)) return;  // uniform across the grid
+    const int64_t n = st.n;
+    const int lane = threadIdx.x & 31, sub = lane & 3;
+    const int64_t i0 = (int64_t)blockIdx.x * (kScreenThreads / 4) + (threadIdx.x >> 2);
+    const bool valid = i0 < n;
+    const int64_t i = valid ? i0 : 0;
+    DevScalars *sc = s.sc;
+    const float band_abs = sc->band_abs;
+    const float4 a0 = s.rec[i], a1 = s.rec[n + i];
+    const int vc = valid ? s.vcnt[i] : 0;
+    const int32_t *vl = s.vlist + i * cap;
+    int32_t *nl = s.nbr + i * cap;
+    const unsigned gshift = lane & ~3u;
+    int pos = 0;
+    unsigned long long nre = 0;
+    float sum = 0.f, comp = 0.f;
+    int jn = sub < vc ? vl[sub] : 0;
+    // every lane runs to the warp's longest list: the ballot below needs the
+    // whole warp (a lane past its own list tests an old, valid j and drops it)
+    const int vmax = __reduce_max_sync(0xffffffffu, vc);
+    for (int k0 = 0; k0 < vmax; k0 += 4) {
+        const int k = k0 + sub;
+        const bool kv = k < vc;
+        const int j = jn;
+        if (k + 4 < vc) jn = vl[k + 4];
+        const float4 b0 = s.rec[j], b1 = s.rec[n + j];
+        const float dx = (a0.x - b0.x) + (a1.x - b1.x);
+        const float dy = (a0.y - b0.y) + (a1.y - b1.y);
+        const float dz = (a0.z - b0.z) + (a1.z - b1.z);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float hs = a0.w + b0.w;
+        const float hs2 = hs * hs;
+        const float d = r2 - hs2;
+        const float M = fmaf(kBandRel, r2 + hs2, band_abs * hs);
+        bool in = d < -M;
+        if (kv && fabsf(d) <= M) {
+            ++nre;
+            in = pair_in_fp64(s.xs[i], s.ys[i], s.zs[i], s.hs[i], s.xs[j], s.ys[j], s.zs[j],
+                              s.hs[j]);
+        }
+        in = in && kv;
+        const unsigned bits = (__ballot_sync(0xffffffffu, in) >> gshift) & 0xfu;
+        if (in) nl[pos + __popc(bits & ((1u << sub) - 1u))] = j;
+        pos += __popc(bits);
+    }
+    if (DENSITY) {
+        // density over the exact list just written (visible to the warp after
+        // the barrier), lane sub taking entries sub, sub + 4, ...: its order
+        // depends on the exact list only, not on which candidate list held it
+        __syncwarp();
+        int jd = sub < pos ? nl[sub] : 0;
+        for (int k = sub; k < pos; k += 4) {
+            const int j = jd;
+            if (k + 4 < pos) jd = nl[k + 4];
+            const float4 b0 = s.rec[j], b1 = s.rec[n + j];
+            const float dx = (a0.x - b0.x) + (a1.x - b1.x);
+            const float dy = (a0.y - b0.y) + (a1.y - b1.y);
+            const float dz = (a0.z - b0.z) + (a1.z - b1.z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float r = r2 * rsqrtf(fmaxf(r2, 1.17549435e-38f));
+            const float hinv = __fdividef(2.f, a0.w + b0.w);  // 1/h_ab
+            const float qq = r * hinv;
+            const float sig = hinv * hinv * hinv * kInvPiF;
+            const float t = 2.f - qq;
+            const float W = qq < 1.f ? sig * fmaf(qq * qq, fmaf(0.75f, qq, -1.5f), 1.f)
+                                     : sig * 0.25f * t * t * t;
+            const float y = b1.w * W - comp;
+            const float tt = sum + y;
+            comp = (tt - sum) - y;
+            sum = tt;
+        }
+        for (int o = 1; o < 4; o <<= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            comp += __shfl_xor_sync(0xffffffffu, comp, o);
+        }
+    }
+    const bool lead = valid && sub == 0;
+    if (lead) s.ncnt[i] = pos;
+    unsigned long long pairs = lead ? (unsigned long long)pos : 0ull;
+    int cmax = lead ? pos : 0;
     for (int o = 16; o > 0; o >>= 1) {
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
         nre += __shfl_xor_sync(0xffffffffu, nre, o);
@@ -309,57 +431,17 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos,
         if (nre) atomicAdd(&sc->rechecks, nre);
         atomicMax(&sc->max_count, cmax);
     }
-    if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&sc->err, ERR_CAPACITY);
-    if (!DENSITY) return;
-    // density over the lists just written (visible to the warp after the
-    // barrier): lane 4q + s4 takes neighbours s4, s4 + 4, ... of row q
-    __syncwarp();
-    const int q = lane >> 2, s4 = lane & 3;
-    const int src = 8 * (q & 3);
-    const int c0r = __shfl_sync(0xffffffffu, cnt0, src);
-    const int c1r = __shfl_sync(0xffffffffu, cnt1, src);
-    const bool vq = q < na;
-    const int cnt = vq ? min(q < 4 ? c0r : c1r, cap) : 0;
-    const int64_t i = ar.x + (vq ? q : 0);
-    const float4 pi0 = s_A[w][q][0], pi1 = s_A[w][q][1];
-    const int32_t *lq = s.nbr + i * cap;
-    float sum = 0.f, comp = 0.f;
-    int jn = s4 < cnt ? lq[s4] : 0;
-    for (int k = s4; k < cnt; k += 4) {
-        const int j = jn;
-        if (k + 4 < cnt) jn = lq[k + 4];
-        const float4 b0 = s.rec[j], b1 = s.rec[n + j];
-        const float dx = (pi0.x - b0.x) + (pi1.x - b1.x);
-        const float dy = (pi0.y - b0.y) + (pi1.y - b1.y);
-        const float dz = (pi0.z - b0.z) + (pi1.z - b1.z);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float r = r2 * rsqrtf(fmaxf(r2, 1.17549435e-38f));
-        const float hinv = __fdividef(2.f, pi0.w + b0.w);  // 1/h_ab
-        const float qq = r * hinv;
-        const float sig = hinv * hinv * hinv * kInvPiF;
-        const float t = 2.f - qq;
-        const float W = qq < 1.f ? sig * fmaf(qq * qq, fmaf(0.75f, qq, -1.5f), 1.f)
-                                 : sig * 0.25f * t * t * t;
-        const float y = b1.w * W - comp;
-        const float tt = sum + y;
-        comp = (tt - sum) - y;
-        sum = tt;
-    }
-    for (int o = 1; o < 4; o <<= 1) {
-        sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        comp += __shfl_xor_sync(0xffffffffu, comp, o);
-    }
-    if (s4 != 0 || !vq) return;
+    if (!DENSITY || !lead) return;
 
-    // equation of state of particle i (lane 4q)
-    const float hi = pi0.w;
-    const float D = pi1.w * kInvPiF / (hi * hi * hi) + (sum - comp);
+    // equation of state of particle i
+    const float hi = a0.w;
+    const float D = a1.w * kInvPiF / (hi * hi * hi) + (sum - comp);
     const int c = s.perm[i];
-    const int star = MULTI_STAR ? astar : 0;
+    const int star = st.star ? st.star[c] : 0;
     const float vx = f64_to_f32_rn(st.vx[c]), vy = f64_to_f32_rn(st.vy[c]),
                 vz = f64_to_f32_rn(st.vz[c]);
-    const PosF pos{pi0.x, pi0.y, pi0.z, pi1.x, pi1.y, pi1.z};
-    Prep<float> pr = eos_prep<float>(eos, g, star, D, vx, vy, vz, pos);
+    const PosF posf{a0.x, a0.y, a0.z, a1.x, a1.y, a1.z};
+    Prep<float> pr = eos_prep<float>(eos, g, star, D, vx, vy, vz, posf);
     const float invD = 1.f / D;
     const float PD2 = pr.P * invD * invD;
     const bool solid = s.tys[i] == 1;
@@ -382,28 +464,23 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap, DevEos eos,
     out.rho[c] = to_out(pr.rho);
     out.P[c] = to_out(pr.P);
     out.cs[c] = to_out(pr.cs);
-    out.ncount[c] = cnt;
+    out.ncount[c] = pos;
 }
 
 }  // namespace
 
 void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
                   int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
-                  const DevRates &out, cudaStream_t stream)
+                  const DevRates &out, cudaStream_t stream, int *nlaunch)
 {
     if (nleaves <= 0) return;
     const int nb = (nleaves + kTileWarps - 1) / kTileWarps;
-    if (multi_star) {
-        if (density)
-            k_tiles<true, true><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap, eos, g, out);
-        else
-            k_tiles<true, false><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap, eos, g, out);
-    } else {
-        if (density)
-            k_tiles<false, true><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap, eos, g, out);
-        else
-            k_tiles<false, false><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap, eos, g, out);
-    }
+    if (multi_star) k_tiles<true><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap);
+    else k_tiles<false><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap);
+    const int ns = (int)((st.n + kScreenThreads / 4 - 1) / (kScreenThreads / 4));
+    if (density) k_screen<true><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
+    else k_screen<false><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
+    if (nlaunch) *nlaunch += 2;
 }
 
 }  // namespace sph

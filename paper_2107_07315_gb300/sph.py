@@ -93,7 +93,7 @@ class sph_rates(C.Structure):
 class sph_options(C.Structure):
     _fields_ = [("h_nmin", C.c_int32), ("h_nmax", C.c_int32), ("max_neighbors", C.c_int32),
                 ("lanes_per_particle", C.c_int32), ("use_graph", C.c_int32),
-                ("totals_every", C.c_int32), ("sort_every", C.c_int32)]
+                ("totals_every", C.c_int32), ("sort_every", C.c_int32), ("skin", C.c_double)]
 
 
 _lib = None
@@ -289,7 +289,8 @@ def sph_init(particles: dict, eos: dict, material: dict, metric=None, precision=
         o = sph_options(int(options.get("h_nmin", 0)), int(options.get("h_nmax", 0)),
                         int(options.get("max_neighbors", 0)),
                         int(options.get("lanes_per_particle", 0)), int(options.get("use_graph", 1)),
-                        int(options.get("totals_every", 0)), int(options.get("sort_every", 0)))
+                        int(options.get("totals_every", 0)), int(options.get("sort_every", 0)),
+                        float(options.get("skin", 0.0)))
     if stream is None:
         import torch
 
