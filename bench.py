@@ -33,7 +33,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pair interactions/s of full SPH-elastic RHS, FP32 vs FP64 at stated error"
 N_STAR = 100_000
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # Algorithmic FP32 flops per ordered pair (FMA = 2), counted from the formulas
 # as the kernels evaluate them once per pair: force pass 74 for a fluid pair
@@ -42,6 +41,7 @@ FLOPS_FORCE_PAIR = 74.0
 FLOPS_FORCE_SOLID_EXTRA = 45.0
 FLOPS_DENSITY_PAIR = 22.0
 # FP64 pair kernels run on the FP64 pipe: nominal dense FP64 rate of the GPU
+# (context only; the roofline divides by the rate measured in the same run)
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -217,8 +217,7 @@ class ClockSampler:
 # the mixed force pass is two kernels (all-fluid blocks, blocks with a solid)
 PROFILE_FILES = {
     "force": (("force_mixed_fluid_star1e5.md", "force_mixed_solid_star1e5.md"), "sph_pairs.cu"),
-    "density": (("density_mixed_star1e5.md",), "sph_pairs.cu"),
-    "lists": (("neighbors_star1e5.md",), "sph_build.cu"),
+    "lists": (("tiles_star1e5.md", "screen_star1e5.md"), "sph_tiles.cu"),
 }
 
 
@@ -287,8 +286,11 @@ def run_ours(args):
     # one device buffer; the fields a step changes lead it (one copy each way for e2e)
     dstate, dbuf, step_bytes = sph.device_state_packed(st, dev)
     torch.cuda.synchronize()
+    # measured FP32 / FP64 FMA rates and SM count of this GPU (roofline peaks)
+    rates = sph.sph_peak_rates()
     ctx = sph.sph_init(dstate, eos, I.DEFAULT_MATERIAL, met, prec,
-                       dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=args.sort_every),
+                       dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=args.sort_every,
+                            skin=args.skin),
                        stream=stream.cuda_stream)
     if external is not None:
         sph.sph_set_external(ctx, external)
@@ -365,6 +367,7 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1)
     e2e_pairs = float(sph.sph_stats(ctx)[1] - p_before)
     launches = int(stats1[12] - stats0[12])
+    builds_per_step = float(stats1[18] - stats0[18]) / max(args.steps, 1)
 
     # aggregate over ranks: total pairs, max time
     if ws > 1:
@@ -378,7 +381,7 @@ def run_ours(args):
         return None
 
     value = pairs / (t_ms * 1e-3)
-    rl = rooflines(tim, n, pairs_step, solid_pairs, prec == sph.SPH_MIXED,
+    rl = rooflines(tim, n, pairs_step, solid_pairs, prec == sph.SPH_MIXED, rates,
                    profiled=(args.workload == "star" and n == N_STAR and prec == sph.SPH_MIXED))
     out = {
         "metric": METRIC,
@@ -409,11 +412,19 @@ def run_ours(args):
             "pairs_per_step": pairs_step,
             "stars_per_gpu": nst,
             "sort_every": args.sort_every,
+            "skin": args.skin if args.skin != 0 else 0.1,
+            "library_defaults": {"sort_every": 1, "skin": 0.1},
+            "candidate_builds_per_step": builds_per_step,
             "l2": "flushed between timed steps by a 256 MB write outside the events",
             "parallelism": "independent star per GPU" if ws > 1 else "single GPU",
         },
         "roofline": rl["dominant"],
         "kernels": rl["all"],
+        "peaks": {"fp32_tflops_measured": rates["fp32_tflops"],
+                  "fp64_tflops_measured": rates["fp64_tflops"], "sms": rates["sms"],
+                  "fp32_tflops_nominal": rl["fp32_nominal"],
+                  "how": "sph_peak_rates: 8 independent FMA chains per thread, "
+                         "8 x 256-thread blocks per SM, CUDA events"},
         # the right-hand side alone (sort, tree, lists, density, force), from the
         # CUDA events inside the timed steps; the step adds both kicks
         "rhs_only": _rhs_only(tim, pairs_step),
@@ -457,6 +468,8 @@ def run_ours(args):
         v64 = p64 / (t64 * 1e-3)
         out["fp64"] = {"value": v64, "unit": "pairs/s", "ms_per_step": t64 / args.fp64_steps,
                        "steps": args.fp64_steps, "mixed_speedup": value / v64}
+    if ws == 1 and args.mode_check and args.workload == "star":
+        out["mode_accuracy"] = mode_accuracy(dev, stream)
     if not args.no_cpu_baseline and ws == 1:
         cb, ids, ro = cpu_baseline(st, eos, met, args.cpu_sample)
         out["cpu_baseline"] = cb
@@ -478,57 +491,111 @@ def run_ours(args):
     return out
 
 
-def rooflines(tim, n, pairs_step, solid_pairs, mixed, profiled=True):
-    """Roofline entries of the timed kernels; "dominant" is the slowest.
+def rooflines(tim, n, pairs_step, solid_pairs, mixed, rates, profiled=True):
+    """Roofline entries of the timed kernels; "dominant" is the pair pass.
 
-    Algorithmic work per launch:
-      neighbour lists: bytes = 16 n (FP32 positions+h read) + 4 pairs (list
-        entries written) + 4 n (counts written); HBM-bound.
-      density pass: 22 flops per ordered pair; FP32 (FP64) pipe.
-      force pass: 74 flops per ordered pair + 45 for pairs touching a solid
-        particle; FP32 (FP64) pipe.
+    The pair pass is the neighbour-list stage (candidate-list build when
+    stale, exact screening, in mixed precision the density summation and the
+    equation of state) plus the force kernels.  Its algorithmic work counts
+    true neighbour pairs only: 22 FP32 flops per ordered pair for the density
+    and 74 for the force, plus 45 for pairs touching a solid particle (FMA =
+    2).  Candidate tests that miss are not counted.  Peak: the FP32 (FP64)
+    FMA rate measured in the same run; the nominal SMs x 128 lanes x 2 x
+    sm_max_mhz is given beside it.
     """
     pk, src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    # DRAM counters exist for the profiled workload (the 1e5 star, mixed) only
     traffic_of = (lambda key: traffic_from_profile(key)) if profiled else (lambda key: None)
-    fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    alu_peak = fp32 if mixed else FP64_NOMINAL_TFLOPS
-    alu_src = ("152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, src)
-               if mixed else "nominal dense FP64 rate (%.2f TFLOP/s)" % FP64_NOMINAL_TFLOPS)
-    hbm = float(pk.get("hbm_gbs", 6800.0))
+    fp32_nom = rates["sms"] * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak = rates["fp32_tflops"] if mixed else rates["fp64_tflops"]
+    alu_src = ("%s FMA rate measured by sph_peak_rates in this run (%d SMs; nominal FP32 "
+               "%.1f TFLOP/s at %.0f MHz)" % ("FP32" if mixed else "FP64", rates["sms"],
+                                               fp32_nom, sm_mhz))
     ms = {
         "force": tim[0] / max(tim[1], 1),
-        "density": tim[2] / max(tim[3], 1),
         "lists": tim[8] / max(tim[9], 1),
+        "sort_tree": tim[6] / max(tim[7], 1),
     }
-    entries = {}
-    fl = FLOPS_FORCE_PAIR * pairs_step + FLOPS_FORCE_SOLID_EXTRA * solid_pairs
-    a = fl / (ms["force"] * 1e-3) / 1e12 if ms["force"] > 0 else 0.0
-    entries["force"] = {"bound": "alu", "kernel": "k_force_%s (pair sums + finalize)" %
-                        ("mixed" if mixed else "fp64"), "achieved": a, "peak": alu_peak,
-                        "unit": "TFLOP/s", "frac": a / alu_peak, "kernel_ms": ms["force"],
-                        "work_per_launch": fl, "peak_source": alu_src,
-                        "traffic": traffic_of("force")}
-    fl = FLOPS_DENSITY_PAIR * pairs_step
-    a = fl / (ms["density"] * 1e-3) / 1e12 if ms["density"] > 0 else 0.0
-    entries["density"] = {"bound": "alu", "kernel": "k_density_%s (density sum + EoS)" %
-                          ("mixed" if mixed else "fp64"), "achieved": a, "peak": alu_peak,
-                          "unit": "TFLOP/s", "frac": a / alu_peak, "kernel_ms": ms["density"],
-                          "work_per_launch": fl, "peak_source": alu_src,
-                          "traffic": traffic_of("density")}
-    by = 16.0 * n + 4.0 * pairs_step + 4.0 * n
-    a = by / (ms["lists"] * 1e-3) / 1e9 if ms["lists"] > 0 else 0.0
-    entries["lists"] = {"bound": "hbm", "kernel": "k_neighbors (tree walk + exact lists)",
-                        "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-                        "kernel_ms": ms["lists"], "work_per_launch": by,
-                        "peak_source": "hbm_gbs (%s)" % src,
-                        "traffic": traffic_of("lists")}
-    dom = max(entries, key=lambda k: entries[k]["kernel_ms"])
-    return {"dominant": entries[dom], "all": {k: {"kernel_ms": v["kernel_ms"],
-                                                  "achieved": v["achieved"], "unit": v["unit"],
-                                                  "frac": v["frac"]} for k, v in entries.items()},
-            "sort_tree_ms": tim[6] / max(tim[7], 1)}
+    fl_force = FLOPS_FORCE_PAIR * pairs_step + FLOPS_FORCE_SOLID_EXTRA * solid_pairs
+    fl_dens = FLOPS_DENSITY_PAIR * pairs_step
+    t_pass = ms["lists"] + ms["force"]
+    a = (fl_force + fl_dens) / (t_pass * 1e-3) / 1e12 if t_pass > 0 else 0.0
+    tl, tf = traffic_of("lists"), traffic_of("force")
+    dominant = {"bound": "alu", "kernel": "pair pass: k_tiles + k_screen (lists, density, EoS) "
+                "+ k_force_%s (pair sums, finalize)" % ("mixed" if mixed else "fp64"),
+                "achieved": a, "peak": alu_peak, "unit": "TFLOP/s", "frac": a / alu_peak,
+                "kernel_ms": t_pass, "work_per_launch": fl_force + fl_dens,
+                "peak_source": alu_src,
+                "traffic": (tl + tf) if (tl is not None and tf is not None) else None}
+    ent = {}
+    a = fl_force / (ms["force"] * 1e-3) / 1e12 if ms["force"] > 0 else 0.0
+    ent["force"] = {"kernel_ms": ms["force"], "achieved": a, "unit": "TFLOP/s",
+                    "frac": a / alu_peak}
+    a = fl_dens / (ms["lists"] * 1e-3) / 1e12 if ms["lists"] > 0 else 0.0
+    ent["lists"] = {"kernel_ms": ms["lists"], "achieved": a, "unit": "TFLOP/s (density flops)",
+                    "frac": a / alu_peak}
+    ent["sort_tree"] = {"kernel_ms": ms["sort_tree"]}
+    return {"dominant": dominant, "all": ent, "fp32_nominal": fp32_nom,
+            "sort_tree_ms": ms["sort_tree"]}
+
+
+def mode_accuracy(dev, stream, n=20000, nsteps=1200, every=10):
+    """Mixed vs FP64 on the same star at equal radial-mode accuracy: the l = 0
+    frequency fitted to each run's central-density series, their relative
+    difference, and the ratio of their step times (Sec. III.B radial mode)."""
+    import torch
+    from scipy.optimize import curve_fit
+
+    from paper_2107_07315_gb300 import inputs as I
+    from paper_2107_07315_gb300 import sph
+
+    st, eos, met, _ = I.star_state(n, seed=1, amp_l0=1e-2)
+    dt = I.cfl_dt(st, eos)
+    r0 = np.sqrt(st["x"] ** 2 + st["y"] ** 2 + st["z"] ** 2)
+    core = torch.from_numpy(r0 < 0.2 * r0.max()).to(dev)
+    res = {}
+    for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+        d = sph.device_state(st, dev)
+        torch.cuda.synchronize()
+        ctx = sph.sph_init(d, eos, I.DEFAULT_MATERIAL, met, prec, dict(use_graph=1, sort_every=8),
+                           stream=stream.cuda_stream)
+        rates = sph.alloc_rates(n, dev)
+        ms, series, t = 0.0, [], []
+        for k in range(0, nsteps + 1, every):
+            if k:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    sph.sph_step(ctx, dt, every)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+            with torch.cuda.stream(stream):
+                sph.sph_rhs(ctx, rates)
+            sph.sph_sync(ctx)
+            t.append(k * dt)
+            series.append(float(rates["rho"][core].mean().item()))
+        sph.sph_free(ctx)
+        y = np.array(series) - np.mean(series)
+        tt = np.array(t)
+        f = np.fft.rfftfreq(len(tt), tt[1] - tt[0])
+        amp = np.abs(np.fft.rfft(y * np.hanning(len(y))))
+        w0 = 2 * math.pi * f[1 + np.argmax(amp[1:])]
+
+        def model(x, a, w, ph, g, c0, c1):
+            return a * np.exp(-g * x) * np.sin(w * x + ph) + c0 + c1 * x
+
+        p, _ = curve_fit(model, tt, y, p0=[np.abs(y).max(), w0, 0.0, 0.0, 0.0, 0.0], maxfev=20000)
+        res[name] = {"omega": abs(float(p[1])), "ms_per_step": ms / nsteps}
+    return {"star_particles": n, "steps": nsteps, "sample_every": every,
+            "omega_mixed": res["mixed"]["omega"], "omega_fp64": res["fp64"]["omega"],
+            "rel_diff": abs(res["mixed"]["omega"] / res["fp64"]["omega"] - 1.0),
+            "tolerance": 1e-3,
+            "mixed_ms_per_step": res["mixed"]["ms_per_step"],
+            "fp64_ms_per_step": res["fp64"]["ms_per_step"],
+            "speedup": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
+            "note": "l = 0 mode of a 2e4-particle TOV star (amplitude 1e-2 c_s), frequencies "
+                    "fitted to the central-density series of each precision's own run"}
 
 
 def _rhs_only(tim, pairs_step):
@@ -724,6 +791,10 @@ def main():
                     help="timed steps of the plain FP64 path on the same star (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count-solid", type=int, default=1)
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="candidate-list skin (0: library default 0.1; < 0: build every RHS)")
+    ap.add_argument("--mode-check", type=int, default=1,
+                    help="also measure the mixed/FP64 speed-up at equal radial-mode accuracy")
     ap.add_argument("--sort-every", type=int, default=8,
                     help="curve sort every k steps (tree and lists are rebuilt every step)")
     args = ap.parse_args()

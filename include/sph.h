@@ -295,6 +295,15 @@ sph_status sph_neighbors_noalloc(int64_t n, const double *x, const double *y, co
                                  const double *h, int64_t *offsets, int32_t *idx, int64_t cap,
                                  void *cuda_stream);
 
+/* Measured FP32 and FP64 fused multiply-add rates of the current device, the
+ * peaks against which the pair kernels' throughput is reported (library
+ * service, no counterpart in the paper).  out (host double[4]): 0 FP32 and
+ * 1 FP64 TFLOP/s (eight independent FMA chains per thread over 8 blocks of
+ * 256 threads per SM, timed with CUDA events after a warm-up), 2 the number
+ * of SMs, 3 zero.  Allocates and frees a small device buffer.  Synchronous.
+ * Errors: SPH_ERR_ARG (NULL out), SPH_ERR_NODEVICE, SPH_ERR_CUDA. */
+sph_status sph_peak_rates(double out[4]);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char *sph_last_error(void);
 

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sph_build.cu", "sph_tiles.cu", "sph_pairs.cu", "sph_step.cu", "sph_api.cu",
-           "sph_noalloc.cu"]
+           "sph_noalloc.cu", "sph_peak.cu"]
 
 
 def _nvcc() -> str:

@@ -37,11 +37,12 @@
 // Exact lists (k_screen), every right-hand side: four lanes per particle take
 // every fourth candidate, test it in FP32 on the two-float positions and,
 // inside the error band, with the FP64 predicate; hits are written at their
-// rank (ascending) and counted.  In mixed precision the four lanes then take
-// every fourth entry of the exact list, sum m_b W(r_ab, h_ab) in a compensated
-// (Kahan) sum per lane and combine in a fixed order, so the density does not
-// depend on which candidate list held the pairs; the self term is added and
-// the equation of state (Eq. poly_eos, Sec. II.A) and rho = D/(sqrt(gamma) W)
+// rank (ascending) and counted.  In mixed precision each hit's m_b W(r_ab,
+// h_ab) goes to the lane that owns its rank in the exact list modulo 4, which
+// sums its hits in rank order in a compensated (Kahan) sum; the four lanes
+// combine in a fixed order.  The density so depends on the exact list only,
+// not on which candidate list held the pairs.  The self term is added and the
+// equation of state (Eq. poly_eos, Sec. II.A) and rho = D/(sqrt(gamma) W)
 // (Sec. I.C) evaluated.
 //
 // FP32 screening bands.  Positions are Xhi + Xlo with Xhi on a grid g (a power
@@ -337,7 +338,7 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
 // memory: every entry is written at or before the last one read.
 constexpr int kScreenThreads = 128;
 template <bool DENSITY>
-__global__ void __launch_bounds__(kScreenThreads, 12)
+__global__ void __launch_bounds__(kScreenThreads, 8)
 k_screen(DevState st, Scratch s, int cap, DevEos eos, DevMetric g, DevRates out)
 {
     if (order_invalid(s.sc)) return;  // uniform across the grid
@@ -356,16 +357,25 @@ k_screen(DevState st, Scratch s, int cap, DevEos eos, DevMetric g, DevRates out)
     int pos = 0;
     unsigned long long nre = 0;
     float sum = 0.f, comp = 0.f;
-    int jn = sub < vc ? vl[sub] : 0;
-    // every lane runs to the warp's longest list: the ballot below needs the
-    // whole warp (a lane past its own list tests an old, valid j and drops it)
+    // every lane runs to the warp's longest list: the ballot and shuffle below
+    // need the whole warp (a lane past its own list tests an old, valid j and
+    // drops it).  The records of the next candidate are loaded one iteration
+    // ahead, its index two ahead, so two gathers per lane are in flight.
     const int vmax = __reduce_max_sync(0xffffffffu, vc);
+    int jn = sub < vc ? vl[sub] : 0;
+    float4 n0 = s.rec[jn], n1 = s.rec[n + jn];
+    int jnn = sub + 4 < vc ? vl[sub + 4] : 0;
     for (int k0 = 0; k0 < vmax; k0 += 4) {
         const int k = k0 + sub;
         const bool kv = k < vc;
         const int j = jn;
-        if (k + 4 < vc) jn = vl[k + 4];
-        const float4 b0 = s.rec[j], b1 = s.rec[n + j];
+        const float4 b0 = n0, b1 = n1;
+        jn = jnn;
+        if (k + 4 < vc) {
+            n0 = s.rec[jn];
+            n1 = s.rec[n + jn];
+        }
+        jnn = k + 8 < vc ? vl[k + 8] : 0;
         const float dx = (a0.x - b0.x) + (a1.x - b1.x);
         const float dy = (a0.y - b0.y) + (a1.y - b1.y);
         const float dz = (a0.z - b0.z) + (a1.z - b1.z);
@@ -382,35 +392,43 @@ k_screen(DevState st, Scratch s, int cap, DevEos eos, DevMetric g, DevRates out)
         }
         in = in && kv;
         const unsigned bits = (__ballot_sync(0xffffffffu, in) >> gshift) & 0xfu;
+        const int nh = __popc(bits);
         if (in) nl[pos + __popc(bits & ((1u << sub) - 1u))] = j;
-        pos += __popc(bits);
-    }
-    if (DENSITY) {
-        // density over the exact list just written (visible to the warp after
-        // the barrier), lane sub taking entries sub, sub + 4, ...: its order
-        // depends on the exact list only, not on which candidate list held it
-        __syncwarp();
-        int jd = sub < pos ? nl[sub] : 0;
-        for (int k = sub; k < pos; k += 4) {
-            const int j = jd;
-            if (k + 4 < pos) jd = nl[k + 4];
-            const float4 b0 = s.rec[j], b1 = s.rec[n + j];
-            const float dx = (a0.x - b0.x) + (a1.x - b1.x);
-            const float dy = (a0.y - b0.y) + (a1.y - b1.y);
-            const float dz = (a0.z - b0.z) + (a1.z - b1.z);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (DENSITY) {
+            // m_b W(r_ab, h_ab) of this lane's candidate (used if it is a hit)
             const float r = r2 * rsqrtf(fmaxf(r2, 1.17549435e-38f));
-            const float hinv = __fdividef(2.f, a0.w + b0.w);  // 1/h_ab
+            const float hinv = __fdividef(2.f, hs);  // 1/h_ab
             const float qq = r * hinv;
             const float sig = hinv * hinv * hinv * kInvPiF;
             const float t = 2.f - qq;
             const float W = qq < 1.f ? sig * fmaf(qq * qq, fmaf(0.75f, qq, -1.5f), 1.f)
                                      : sig * 0.25f * t * t * t;
-            const float y = b1.w * W - comp;
-            const float tt = sum + y;
-            comp = (tt - sum) - y;
-            sum = tt;
+            const float term = b1.w * W;
+            // lane sub sums the hits whose rank in the exact list is sub mod 4,
+            // in rank order: the same sums as a pass over the exact list, so
+            // the density does not depend on which candidate list held them.
+            // This round's hits hold ranks pos .. pos + nh - 1; the one of rank
+            // = sub (mod 4) is hit number idx, on lane src of the group.
+            const int idx = (sub - pos) & 3;
+            int src = sub, c = 0;
+#pragma unroll
+            for (int bq = 0; bq < 4; ++bq) {
+                if ((bits >> bq) & 1u) {
+                    if (c == idx) src = bq;
+                    ++c;
+                }
+            }
+            const float tv = __shfl_sync(0xffffffffu, term, (int)gshift + src);
+            if (idx < nh) {
+                const float y = tv - comp;
+                const float tt = sum + y;
+                comp = (tt - sum) - y;
+                sum = tt;
+            }
         }
+        pos += nh;
+    }
+    if (DENSITY) {
         for (int o = 1; o < 4; o <<= 1) {
             sum += __shfl_xor_sync(0xffffffffu, sum, o);
             comp += __shfl_xor_sync(0xffffffffu, comp, o);

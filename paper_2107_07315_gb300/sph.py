@@ -27,7 +27,7 @@ STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
 EXPORTS = ("sph_init", "sph_rhs", "sph_step", "sph_sync", "sph_neighbors", "sph_totals",
            "sph_stats", "sph_timing", "sph_timing_read", "sph_state_size", "sph_get_state",
            "sph_set_state", "sph_free", "sph_last_error", "sph_neighbors_noalloc",
-           "sph_set_external", "sph_relax_finish", "sph_set_wait_limit")
+           "sph_set_external", "sph_relax_finish", "sph_set_wait_limit", "sph_peak_rates")
 
 
 class SphError(RuntimeError):
@@ -114,6 +114,7 @@ def lib():
         L.sph_step.argtypes = [vp, C.c_double, C.c_int32]
         L.sph_sync.argtypes = [vp]
         L.sph_set_wait_limit.argtypes = [vp, C.c_int32]
+        L.sph_peak_rates.argtypes = [_d]
         L.sph_neighbors.argtypes = [vp, vp, vp, C.c_int64]
         L.sph_totals.argtypes = [vp, _d]
         L.sph_stats.argtypes = [vp, _i64]
@@ -333,6 +334,13 @@ def sph_relax_finish(ctx: SphCtx, eos: dict) -> None:
 
 def sph_sync(ctx: SphCtx) -> None:
     _check(lib().sph_sync(ctx.handle), "sph_sync")
+
+
+def sph_peak_rates() -> dict:
+    """Measured FP32/FP64 FMA rates (TFLOP/s) and SM count of the current device."""
+    out = np.zeros(4, np.float64)
+    _check(lib().sph_peak_rates(out.ctypes.data_as(_d)), "sph_peak_rates")
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "sms": int(out[2])}
 
 
 def sph_set_wait_limit(ctx: SphCtx, polls: int) -> None:
