@@ -369,6 +369,17 @@ def run_ours(args):
     launches = int(stats1[12] - stats0[12])
     builds_per_step = float(stats1[18] - stats0[18]) / max(args.steps, 1)
 
+    # the ensemble's only data collective: the per-star FP64 totals, gathered
+    # from every rank (each star lives on one rank); every rank takes part
+    star_totals = None
+    if args.workload == "ensemble":
+        from paper_2107_07315_gb300 import shard
+
+        per = sph.sph_totals_per_star(ctx, nst)
+        allt = shard.gather_star_totals(mine, per, args.nstars, dev)
+        star_totals = {"stars": int(args.nstars), "mass": float(allt[:, 0].sum()),
+                       "energy": float(allt[:, 6].sum()), "yielded": float(allt[:, 10].sum()),
+                       "broken": float(allt[:, 11].sum())}
     # aggregate over ranks: total pairs, max time
     if ws > 1:
         from paper_2107_07315_gb300 import shard
@@ -468,6 +479,8 @@ def run_ours(args):
         v64 = p64 / (t64 * 1e-3)
         out["fp64"] = {"value": v64, "unit": "pairs/s", "ms_per_step": t64 / args.fp64_steps,
                        "steps": args.fp64_steps, "mixed_speedup": value / v64}
+    if star_totals is not None:
+        out["star_totals"] = star_totals
     if ws == 1 and args.mode_check and args.workload == "star":
         out["mode_accuracy"] = mode_accuracy(dev, stream)
     if not args.no_cpu_baseline and ws == 1:

@@ -217,7 +217,17 @@ sph_status sph_neighbors(sph_ctx *ctx, int64_t *offsets, int32_t *idx, int64_t c
  * mass.  Synchronous. */
 sph_status sph_totals(sph_ctx *ctx, double out[16]);
 
-/* Counters (host out[16]): 0 ordered neighbour pairs of the last right-hand
+/* Totals of each star separately, the quantities of sph_totals over the
+ * particles of star s only (star index of sph_particles; all particles form
+ * star 0 when it is NULL): host out[nstars * 16], row s holding star s.
+ * Each star is reduced in FP64 over its particles in ascending caller
+ * index, in a fixed order, so the result does not depend on the curve order.
+ * These are what the batched ensemble gathers from several GPUs.
+ * Synchronous.  Errors: SPH_ERR_ARG (NULL, nstars differs from the
+ * context's), SPH_ERR_CUDA. */
+sph_status sph_totals_per_star(sph_ctx *ctx, double *out, int32_t nstars);
+
+/* Counters (host out[24]): 0 ordered neighbour pairs of the last right-hand
  * side, 1 pairs summed over all right-hand sides, 2 right-hand sides
  * evaluated, 3 kernel launches in the last step, 4 tree leaves, 5 marginal pairs
  * re-checked in FP64 (cumulative), 6 neighbour capacity per particle,

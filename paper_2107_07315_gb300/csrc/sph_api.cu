@@ -78,6 +78,9 @@ struct sph_ctx {
     DevRates r{};
     double *vp = nullptr, *Sp = nullptr;
     double *tot_partial = nullptr, *tot_out = nullptr;
+    int64_t *star_off = nullptr;                       // per-star caller indices (CSR)
+    int32_t *star_idx = nullptr;
+    double *star_tot = nullptr;                        // [nstars][16]
     double *zeros = nullptr;  // stand-in for absent per-particle material arrays
     int have_rates = 0;
     int64_t steps = 0;
@@ -675,6 +678,19 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     STATUS_TRY(c->alloc(&c->tot_partial, 16 * kTotalsBlocks));
     STATUS_TRY(c->alloc(&c->tot_out, 16));
     STATUS_TRY(c->alloc(&c->zeros, nn));
+    {
+        // caller indices of each star, ascending (per-star totals)
+        std::vector<int64_t> off(c->nstars + 1, 0);
+        for (int s2 = 0; s2 < c->nstars; ++s2) off[s2 + 1] = off[s2] + per[s2];
+        std::vector<int32_t> idx(nn, 0), fill(off.begin(), off.end() - 1);
+        for (int64_t i = 0; i < n; ++i) idx[fill[star[i]]++] = (int32_t)i;
+        STATUS_TRY(c->alloc(&c->star_off, off.size()));
+        STATUS_TRY(c->alloc(&c->star_idx, nn));
+        STATUS_TRY(c->alloc(&c->star_tot, (size_t)c->nstars * 16));
+        CUDA_TRY(cudaMemcpy(c->star_off, off.data(), off.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->star_idx, idx.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(cudaMemset(c->zeros, 0, nn * sizeof(double)));
     // EoS, material, metric.
     STATUS_TRY(upload_eos(c, eos));
@@ -998,6 +1014,21 @@ sph_status sph_totals(sph_ctx *c, double out[16])
     StepState ss = step_state_of(c);
     launch_totals(ss, c->have_rates ? c->r.ncount : nullptr, c->tot_partial, c->tot_out, c->stream);
     CUDA_TRY(cudaMemcpyAsync(out, c->tot_out, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+sph_status sph_totals_per_star(sph_ctx *c, double *out, int32_t nstars)
+{
+    if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
+    if (nstars != c->nstars)
+        return fail(SPH_ERR_ARG, "nstars = %d, the context holds %d stars", nstars, c->nstars);
+    StepState ss = step_state_of(c);
+    launch_star_totals(ss, c->have_rates ? c->r.ncount : nullptr, c->nstars, c->star_off,
+                       c->star_idx, c->star_tot, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out, c->star_tot, (size_t)nstars * 16 * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return SPH_OK;
 }

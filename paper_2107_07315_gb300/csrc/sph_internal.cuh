@@ -295,6 +295,10 @@ void launch_kick_return(const StepState &s, const DevRates &r, const DevEos &eos
 constexpr int kTotalsBlocks = 256;
 void launch_totals(const StepState &s, const int32_t *ncount, double *partial, double *out,
                    cudaStream_t st);
+// FP64 totals of each star (out[nstars][16]) over the caller indices of each
+// star, idx[off[s] .. off[s+1]) ascending.
+void launch_star_totals(const StepState &s, const int32_t *ncount, int nstars,
+                        const int64_t *off, const int32_t *idx, double *out, cudaStream_t st);
 void launch_export_counts(const Scratch &s, int64_t n, int64_t *counts_out,
                           cudaStream_t st);
 // Neighbour lists of the last right-hand side in caller order and ascending

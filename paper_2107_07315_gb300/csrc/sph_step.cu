@@ -220,6 +220,62 @@ __global__ void k_totals_sum(const double *partial, int nblocks, int64_t n, doub
     for (int k = 0; k < 16; ++k) out[k] = t[k];
 }
 
+// FP64 totals of each star (one block per star, over the star's caller
+// indices in ascending order, fixed reduction order): the quantities of
+// k_totals_partial/k_totals_sum for the star's particles alone.
+__global__ void k_star_totals(StepState s, const int32_t *ncount, const int64_t *off,
+                              const int32_t *idx, double *out)
+{
+    __shared__ double red[16][kTotThreads / 32];
+    const int st = blockIdx.x;
+    double acc[16];
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    for (int64_t p = off[st] + threadIdx.x; p < off[st + 1]; p += blockDim.x) {
+        const int64_t a = idx[p];
+        double m = s.m[a];
+        double v[3] = {s.vx[a], s.vy[a], s.vz[a]};
+        double x[3] = {s.x[a], s.y[a], s.z[a]};
+        acc[0] += m;
+        acc[1] += m * v[0];
+        acc[2] += m * v[1];
+        acc[3] += m * v[2];
+        acc[4] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        acc[5] += m * s.u[a];
+        acc[7] += m * (x[1] * v[2] - x[2] * v[1]);
+        acc[8] += m * (x[2] * v[0] - x[0] * v[2]);
+        acc[9] += m * (x[0] * v[1] - x[1] * v[0]);
+        uint8_t f = s.flags[a];
+        acc[10] += (f & 1u) ? 1.0 : 0.0;
+        acc[11] += (f & 2u) ? 1.0 : 0.0;
+        acc[12] += ncount ? (double)ncount[a] : 0.0;
+        acc[13] += m * x[0];
+        acc[14] += m * x[1];
+        acc[15] += m * x[2];
+    }
+    for (int k = 0; k < 16; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double t[16];
+    for (int k = 0; k < 16; ++k) {
+        double v = 0.0;
+        for (int w = 0; w < kTotThreads / 32; ++w) v += red[k][w];
+        t[k] = v;
+    }
+    const double cnt = (double)(off[st + 1] - off[st]);
+    t[6] = t[4] + t[5];
+    t[12] = cnt > 0.0 ? t[12] / cnt : 0.0;
+    if (t[0] > 0.0) {
+        t[13] /= t[0];
+        t[14] /= t[0];
+        t[15] /= t[0];
+    }
+    for (int k = 0; k < 16; ++k) out[st * 16 + k] = t[k];
+}
+
 __global__ void k_export_counts(const int32_t *perm, const int32_t *ncnt, int64_t n,
                                 int64_t *counts_out)
 {
@@ -306,6 +362,13 @@ void launch_totals(const StepState &s, const int32_t *ncount, double *partial, d
 {
     k_totals_partial<<<kTotBlocks, kTotThreads, 0, st>>>(s, ncount, partial);
     k_totals_sum<<<1, 32, 0, st>>>(partial, kTotBlocks, s.n, out);
+}
+
+void launch_star_totals(const StepState &s, const int32_t *ncount, int nstars,
+                        const int64_t *off, const int32_t *idx, double *out, cudaStream_t st)
+{
+    if (nstars < 1) return;
+    k_star_totals<<<nstars, kTotThreads, 0, st>>>(s, ncount, off, idx, out);
 }
 
 void launch_export_counts(const Scratch &s, int64_t n, int64_t *counts_out, cudaStream_t st)

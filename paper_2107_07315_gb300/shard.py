@@ -1,7 +1,8 @@
 """Host logic for runs on several GPUs of one node.
 
 Stars are independent problems: each rank advances its own subset with no
-data-path exchange.  The only collectives are the timing/accounting
+data-path exchange.  The collectives are the final gather of the per-star
+FP64 totals (each star is owned by one rank) and the timing/accounting
 reductions of the benchmark (max of the ranks' times, sum of their pairs).
 """
 from __future__ import annotations
@@ -39,3 +40,25 @@ def reduce_timing(t_ms: float, pairs: float, device=None):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(p, op=dist.ReduceOp.SUM)
     return float(t.item()), float(p.item())
+
+
+def gather_star_totals(star_ids, totals, nstars: int, device=None) -> np.ndarray:
+    """Per-star FP64 totals of all ranks, [nstars, 16] on every rank.
+
+    star_ids: the global ids of this rank's stars; totals: their rows
+    (sph_totals_per_star of this rank's context, in the same order).  Each
+    star belongs to exactly one rank, so the exchange is a sum of arrays that
+    are zero outside each rank's rows: exact, whatever the reduction order.
+    """
+    import torch
+    import torch.distributed as dist
+
+    out = np.zeros((nstars, 16), np.float64)
+    out[np.asarray(star_ids, dtype=np.int64)] = np.asarray(totals, dtype=np.float64)
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return out
+    t = torch.from_numpy(out)
+    if device is not None:
+        t = t.to(device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy()

@@ -27,7 +27,8 @@ STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
 EXPORTS = ("sph_init", "sph_rhs", "sph_step", "sph_sync", "sph_neighbors", "sph_totals",
            "sph_stats", "sph_timing", "sph_timing_read", "sph_state_size", "sph_get_state",
            "sph_set_state", "sph_free", "sph_last_error", "sph_neighbors_noalloc",
-           "sph_set_external", "sph_relax_finish", "sph_set_wait_limit", "sph_peak_rates")
+           "sph_set_external", "sph_relax_finish", "sph_set_wait_limit", "sph_peak_rates",
+           "sph_totals_per_star")
 
 
 class SphError(RuntimeError):
@@ -115,6 +116,7 @@ def lib():
         L.sph_sync.argtypes = [vp]
         L.sph_set_wait_limit.argtypes = [vp, C.c_int32]
         L.sph_peak_rates.argtypes = [_d]
+        L.sph_totals_per_star.argtypes = [vp, _d, C.c_int32]
         L.sph_neighbors.argtypes = [vp, vp, vp, C.c_int64]
         L.sph_totals.argtypes = [vp, _d]
         L.sph_stats.argtypes = [vp, _i64]
@@ -354,6 +356,14 @@ def sph_neighbors(ctx: SphCtx, offsets, idx, cap: int) -> None:
 def sph_totals(ctx: SphCtx) -> np.ndarray:
     out = np.zeros(16, np.float64)
     _check(lib().sph_totals(ctx.handle, out.ctypes.data_as(_d)), "sph_totals")
+    return out
+
+
+def sph_totals_per_star(ctx: SphCtx, nstars: int) -> np.ndarray:
+    """FP64 totals of each star: array [nstars, 16] (columns as sph_totals)."""
+    out = np.zeros((nstars, 16), np.float64)
+    _check(lib().sph_totals_per_star(ctx.handle, out.ctypes.data_as(_d), int(nstars)),
+           "sph_totals_per_star")
     return out
 
 

@@ -35,6 +35,32 @@ def test_ensemble_batch_vs_oracle(ensemble, prec, tol):
     assert_close(g, o, tol, label="ensemble")
 
 
+def test_star_totals_per_star_match_oracle(ensemble):
+    # per-star FP64 totals of the batch, after 3 steps, against the oracle's
+    # totals of each star's particles (and their sum against sph_totals)
+    st, eos, met, params = ensemble
+    dev = sph.device_state(st)
+    torch.cuda.synchronize()
+    ctx = sph.sph_init(dev, eos, MAT, met, sph.SPH_FP64, stream=stream().cuda_stream)
+    dt = 0.5 * I.cfl_dt(st, eos)
+    sph.sph_step(ctx, dt, 3)
+    sph.sph_sync(ctx)
+    g = sph.to_numpy(dev)
+    per = sph.sph_totals_per_star(ctx, 6)
+    rates = sph.alloc_rates(len(st["x"]))
+    for s_id in range(6):
+        sel = g["star"] == s_id
+        sub = {k: (v[..., sel] if v is not None else None) for k, v in g.items()}
+        o = oracle.totals(sub)
+        for k in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 13, 14, 15):
+            assert abs(per[s_id, k] - o[k]) <= 1e-12 * max(abs(o[k]), 1e-300) + 1e-14 * abs(o[0]), (s_id, k)
+        assert per[s_id, 10] == o[10] and per[s_id, 11] == o[11]
+    tot = sph.sph_totals(ctx)
+    assert abs(per[:, 0].sum() - tot[0]) <= 1e-13 * tot[0]
+    with pytest.raises(sph.SphError):
+        sph.sph_totals_per_star(ctx, 5)
+
+
 def test_ensemble_sort_every_keeps_lists(ensemble):
     # multi-star batch: steps that keep the last curve order (sort_every = 4)
     # give the same lists as sorting every step, and states equal to rounding

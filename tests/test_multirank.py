@@ -63,3 +63,51 @@ def test_two_rank_timing_reduction_gloo():
     for _, _, t, p in res:
         assert t == 11.0
         assert p == 150.0 * 60.0
+
+
+def _star_worker(rank, ws, port, q):
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2107_07315_gb300 import inputs as I
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        st, _, _, params = I.ensemble_state(nstars=5, seed=11, n_lo=300, n_hi=900, nr=64)
+        mine = shard.assign_stars(params["N"], ws)[rank]
+        rows = []
+        for s_id in mine:
+            sel = st["star"] == s_id
+            sub = {k: (v[..., sel] if v is not None else None) for k, v in st.items()}
+            rows.append(oracle.totals(sub))
+        q.put((rank, shard.gather_star_totals(mine, rows, 5)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_star_totals_gather_equals_single_process():
+    import torch.multiprocessing as mp
+
+    import oracle
+    from paper_2107_07315_gb300 import inputs as I
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_star_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=180) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # the single-process result: every star's totals in one place
+    st, _, _, _ = I.ensemble_state(nstars=5, seed=11, n_lo=300, n_hi=900, nr=64)
+    ref = np.zeros((5, 16))
+    for s_id in range(5):
+        sel = st["star"] == s_id
+        ref[s_id] = oracle.totals({k: (v[..., sel] if v is not None else None) for k, v in st.items()})
+    for _, got in res:
+        assert np.array_equal(got, ref)
