@@ -214,19 +214,30 @@ class ClockSampler:
                 "samples": len(sm), "source": "nvidia-smi, 200 ms period"}
 
 
-# the mixed force pass is two kernels (all-fluid blocks, blocks with a solid)
+# the mixed force pass is two kernels (all-fluid blocks, blocks with a solid);
+# each entry names the summaries and the sources their kernels are built from
 PROFILE_FILES = {
-    "force": (("force_mixed_fluid_star1e5.md", "force_mixed_solid_star1e5.md"), "sph_pairs.cu"),
-    "lists": (("tiles_star1e5.md", "screen_star1e5.md"), "sph_tiles.cu"),
+    "force": (("force_mixed_fluid_star1e5.md", "force_mixed_solid_star1e5.md"),
+              ("sph_pairs.cu", "sph_device.cuh")),
+    "lists": (("tiles_star1e5.md", "screen_star1e5.md"),
+              ("sph_tiles.cu", "sph_screen.cuh", "sph_device.cuh")),
 }
+
+
+def source_hash(srcs) -> str:
+    """First 16 hex digits of the SHA-256 of the named kernel sources, in order."""
+    hs = hashlib.sha256()
+    for src in srcs:
+        with open(os.path.join(ROOT, "paper_2107_07315_gb300", "csrc", src), "rb") as f:
+            hs.update(f.read())
+    return hs.hexdigest()[:16]
 
 
 def traffic_from_profile(key: str):
     """DRAM bytes per pass from the committed ncu summaries of its kernels,
-    or None when their source changed since the counters were taken."""
-    names, src = PROFILE_FILES[key]
-    kernel_src = os.path.join(ROOT, "paper_2107_07315_gb300", "csrc", src)
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    or None when their sources changed since the counters were taken."""
+    names, srcs = PROFILE_FILES[key]
+    h = source_hash(srcs)
     total = 0.0
     for name in names:
         path = os.path.join(ROOT, "profiles", name)
@@ -290,10 +301,12 @@ def run_ours(args):
     rates = sph.sph_peak_rates()
     ctx = sph.sph_init(dstate, eos, I.DEFAULT_MATERIAL, met, prec,
                        dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=args.sort_every,
-                            skin=args.skin),
+                            skin=args.skin, lanes_per_particle=-1 if args.tune else 0,
+                            persistent=-1 if args.tune else args.persistent),
                        stream=stream.cuda_stream)
     if external is not None:
         sph.sph_set_external(ctx, external)
+    shape = launch_shape(sph.sph_stats(ctx))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -429,6 +442,7 @@ def run_ours(args):
             "l2": "flushed between timed steps by a 256 MB write outside the events",
             "parallelism": "independent star per GPU" if ws > 1 else "single GPU",
         },
+        "launch_shape": shape,
         "roofline": rl["dominant"],
         "kernels": rl["all"],
         "peaks": {"fp32_tflops_measured": rates["fp32_tflops"],
@@ -449,7 +463,9 @@ def run_ours(args):
     if ws == 1 and args.sort_every > 1:
         # the same protocol with a curve sort on every step, for comparison
         c1 = sph.sph_init(dstate, eos, I.DEFAULT_MATERIAL, met, prec,
-                          dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=1),
+                          dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=1,
+                               lanes_per_particle=-1 if args.tune else 0,
+                               persistent=-1 if args.tune else args.persistent),
                           stream=stream.cuda_stream)
         if external is not None:
             sph.sph_set_external(c1, external)
@@ -787,6 +803,27 @@ def run_reference(args):
     return out
 
 
+def launch_shape(stats):
+    """The launch shape sph_init chose (threads per particle of the exact
+    screening and of the pair kernels, and whether screening and force run as
+    one persistent launch) and the autotuner's per-launch times; the library's
+    fixed default is 4 screening lanes, 8 pair lanes, separate launches."""
+    src = {0: "fixed", 1: "autotuned", 2: "autotuned (process cache)"}[int(stats[20])]
+    out = {"screen_lanes": int(stats[19]), "pair_lanes": int(stats[7]),
+           "persistent_blocks": int(stats[25]), "source": src,
+           "fixed_default": {"screen_lanes": 4, "pair_lanes": 8, "persistent": False}}
+    if stats[26] > 0 and stats[27] > 0:
+        # screening + force of the chosen lanes: separate launches vs one persistent launch
+        out["tuner_us_separate_vs_persistent"] = [int(stats[26]) / 1e3, int(stats[27]) / 1e3]
+    t = [int(v) for v in stats[21:25]]
+    if all(v > 0 for v in t):
+        out["tuner_us_per_launch"] = {"screen_4": t[0] / 1e3, "screen_8": t[1] / 1e3,
+                                      "pairs_4": t[2] / 1e3, "pairs_8": t[3] / 1e3}
+        # screening + pair kernels of the chosen shape against the fixed one
+        out["tuned_vs_fixed"] = (t[0] + t[3]) / (min(t[0], t[1]) + min(t[2], t[3]))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -806,6 +843,11 @@ def main():
     ap.add_argument("--count-solid", type=int, default=1)
     ap.add_argument("--skin", type=float, default=0.0,
                     help="candidate-list skin (0: library default 0.1; < 0: build every RHS)")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="1: autotune the launch shape in sph_init (lane counts and the "
+                         "persistent launch)")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="with --tune 0: 1 runs screening + force as one persistent launch")
     ap.add_argument("--mode-check", type=int, default=1,
                     help="also measure the mixed/FP64 speed-up at equal radial-mode accuracy")
     ap.add_argument("--sort-every", type=int, default=8,

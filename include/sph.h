@@ -139,8 +139,26 @@ typedef struct {
  * max_neighbors: most neighbours a particle may have (1..256); more raise
  * SPH_ERR_CAPACITY at sph_sync [0: 256].
  * lanes_per_particle: 4 or 8 threads share one particle's list in the pair
- * kernels [0: 8]; -1 lets sph_init time both on the bound state and keep
- * the faster (the summation order then depends on that timing).
+ * kernels [0: 8]; -1 turns on the autotuner of the lane counts: sph_init evaluates one
+ * right-hand side on the bound state (writing the rates), then times the
+ * exact screening with 4 and 8 threads per particle and the pair kernels
+ * with 4 and 8, keeps the faster of each and restores the counters.  The
+ * choice is cached for the process under (device, n, stars, precision,
+ * max_neighbors, metric, any solid), so a later context of that
+ * configuration reuses it without timing.  Lane counts set the order of the
+ * density and pair sums: a tuned context agrees with a fixed one to
+ * rounding.  sph_stats reports the shape and the times.
+ * screen_lanes: threads per particle of the exact screening, 4 or 8 [0: 4];
+ * ignored when lanes_per_particle is -1.
+ * persistent: 1 runs the exact screening, density, equation of state and
+ * force pass of every right-hand side as one persistent launch over a global
+ * work queue of particle blocks (screening items first, then force items,
+ * which wait with a bounded poll until every screening item is done; a wait
+ * that runs out gives SPH_ERR_TIMEOUT at sph_sync); mixed precision only,
+ * ignored in FP64; -1 lets sph_init time both forms (of the chosen lane
+ * counts) and keep the faster, cached like the lane counts [0: separate
+ * launches].  Same sums in the same order as the separate launches of the
+ * same lane counts: the rates are identical either way.
  * use_graph: capture each step in a CUDA graph [1].
  * totals_every: compute totals every k steps inside sph_step [0: never].
  * sort_every: sph_step sorts the particles along the space-filling curve on
@@ -164,6 +182,8 @@ typedef struct {
     int32_t totals_every;
     int32_t sort_every;
     double skin;
+    int32_t screen_lanes;
+    int32_t persistent;
 } sph_options;
 
 /* Create a context bound to the particle buffers.  Validates the inputs,
@@ -193,14 +213,16 @@ sph_status sph_step(sph_ctx *ctx, double dt, int32_t nsteps);
  * work, and so do those of later ones until sph_sync clears the error. */
 sph_status sph_sync(sph_ctx *ctx);
 
-/* Bound on the device-side waits of the context's sort: a sort tile that
- * has made `polls` rounds of reads of its predecessors' published counts
- * without finding its prefix (decoupled look-back) gives up and raises the
- * timeout reported by sph_sync.  polls < 0 restores the default (2^22); 0
- * makes every tile after the first give up at once (a way to exercise the
- * timeout path on inputs of more than one sort tile, n > 256).  Library
- * service, no counterpart in the paper.  Synchronous.  Errors: SPH_ERR_ARG
- * (NULL ctx), SPH_ERR_CUDA. */
+/* Bound on the context's device-side waits.  A sort tile that has made
+ * `polls` rounds of reads of its predecessors' published counts without
+ * finding its prefix (decoupled look-back), and a force item of the
+ * persistent launch (options.persistent) that has polled the count of
+ * finished screening items `polls` times, give up and raise the timeout
+ * reported by sph_sync.  polls < 0 restores the default (2^22); 0 makes
+ * every such wait give up at its first poll (a way to exercise the timeout
+ * path: on inputs of more than one sort tile, n > 256, or on a persistent
+ * step without a curve sort).  Library service, no counterpart in the
+ * paper.  Synchronous.  Errors: SPH_ERR_ARG (NULL ctx), SPH_ERR_CUDA. */
 sph_status sph_set_wait_limit(sph_ctx *ctx, int32_t polls);
 
 /* Neighbour lists of the last right-hand side, CSR in caller order with
@@ -227,7 +249,7 @@ sph_status sph_totals(sph_ctx *ctx, double out[16]);
  * context's), SPH_ERR_CUDA. */
 sph_status sph_totals_per_star(sph_ctx *ctx, double *out, int32_t nstars);
 
-/* Counters (host out[24]): 0 ordered neighbour pairs of the last right-hand
+/* Counters (host out[32]): 0 ordered neighbour pairs of the last right-hand
  * side, 1 pairs summed over all right-hand sides, 2 right-hand sides
  * evaluated, 3 kernel launches in the last step, 4 tree leaves, 5 marginal pairs
  * re-checked in FP64 (cumulative), 6 neighbour capacity per particle,
@@ -237,18 +259,27 @@ sph_status sph_totals_per_star(sph_ctx *ctx, double *out, int32_t nstars);
  * 14 most candidate leaves of one leaf and 16 candidate (leaf, leaf) tiles
  * in all (both of the last candidate-list build), 15 most neighbours of one
  * particle (last right-hand side), 17 1 for mixed precision, 18 candidate-list
- * builds so far, 19-23 zero.  Synchronous. */
-sph_status sph_stats(sph_ctx *ctx, int64_t out[24]);
+ * builds so far, 19 lanes per particle of the exact screening, 20 launch
+ * shape source (0 fixed by the options, 1 timed by sph_init, 2 taken from the
+ * process cache), 21-24 the autotuner's times in ns per launch (screening
+ * with 4 and 8 lanes, pair kernels with 4 and 8 lanes; zero when not tuned),
+ * 25 blocks of the persistent right-hand-side launch (0: separate launches),
+ * 26 and 27 the autotuner's times in ns of the screening and pair kernels in
+ * series and of the persistent launch (zero unless persistent is -1),
+ * 28-31 zero.  Synchronous. */
+sph_status sph_stats(sph_ctx *ctx, int64_t out[32]);
 
 /* Device-time measurement with CUDA events on the context's stream.
  * enable 1 starts recording around the kernels of every step or right-hand
  * side; sph_timing_read returns (host out[12]) summed milliseconds and
  * sample counts: 0/1 force kernels, 2/3 FP64 density kernel (zero in mixed
- * precision, where the tile kernel sums the density), 4/5 whole steps (or
- * right-hand sides), 6/7 bounding box through tree (keys, sort, gather,
- * tree), 8/9 pair-tile kernel (candidate leaves, neighbour masks; in mixed
- * precision also the density and equation of state), 10/11 both (6 plus 8).
- * Reading resets the sums.  Synchronous. */
+ * precision, where the screening kernel sums the density), 4/5 whole steps
+ * (or right-hand sides), 6/7 bounding box through tree (keys, sort, gather,
+ * tree), 8/9 neighbour lists (the pair-tile candidate build when stale and
+ * the exact screening; in mixed precision also the density and equation of
+ * state), 10/11 both (6 plus 8).  With the persistent launch 8/9 hold the
+ * candidate build only and 0/1 the persistent launch (screening, density,
+ * equation of state and force).  Reading resets the sums.  Synchronous. */
 sph_status sph_timing(sph_ctx *ctx, int32_t enable);
 sph_status sph_timing_read(sph_ctx *ctx, double out[12]);
 
@@ -291,7 +322,7 @@ void sph_free(sph_ctx *ctx);
  * cuda_stream a cudaStream_t (NULL: legacy default stream).  Scratch is one
  * fixed device array of about 11.9 MB inside the library, present on every
  * GPU that loads it until the process exits.  Limits: n <= 16384 (larger n
- * returns SPH_ERR_ARG), at most 128 neighbours per particle and 512
+ * returns SPH_ERR_ARG), at most 128 neighbours per particle and 256
  * candidate leaves (groups of 8 sorted particles) per leaf
  * (SPH_ERR_CAPACITY); more than cap entries in all returns SPH_ERR_CAPACITY
  * with offsets written and idx not.  Under lazy module loading (the CUDA

@@ -44,7 +44,7 @@ def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     header_deps = [os.path.join(CSRC, "sph_internal.cuh"), os.path.join(CSRC, "sph_device.cuh"),
-                   os.path.join(ROOT, "include", "sph.h")]
+                   os.path.join(CSRC, "sph_screen.cuh"), os.path.join(ROOT, "include", "sph.h")]
     jobs = []
     objs = []
     for src in SOURCES:

@@ -6,7 +6,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "sph_internal.cuh"
@@ -74,7 +78,14 @@ struct sph_ctx {
     TreeLevels tl{};
     int nleaves = 0;
     int cap = 128;
-    int lanes = 8;
+    int lanes = 8;          // threads per particle of the pair kernels
+    int screen_lanes = 4;   // threads per particle of the exact screening
+    int tuned = 0;          // 0 fixed shape, 1 timed by sph_init, 2 from the process cache
+    // autotuner times (ns per launch): screening 4 / 8 lanes, pair kernels
+    // 4 / 8 lanes, screening + pair kernels in series, persistent launch
+    int64_t tune_ns[6] = {};
+    int tune_persist = 0;   // the autotuner chose the persistent launch
+    PersistPlan pplan{};    // persistent right-hand side (grid 0: off)
     DevRates r{};
     double *vp = nullptr, *Sp = nullptr;
     double *tot_partial = nullptr, *tot_out = nullptr;
@@ -342,10 +353,22 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
     rec(c, slot_ev(c, EV_BUILD), capturing);
     launch_build(st, c->s, c->plan, c->tl, c->nleaves, fp64, c->stream, nlaunch, resort);
     rec(c, slot_ev(c, EV_LISTS), capturing);
+    if (c->pplan.grid > 0 && !fp64) {
+        // candidate lists (when stale), then screening, density, equation of
+        // state and force in one persistent launch
+        launch_tiles_build(st, c->s, c->tl, c->nleaves, c->multi, c->cap, c->stream);
+        rec(c, slot_ev(c, EV_DENSITY), capturing);
+        rec(c, slot_ev(c, EV_FORCE), capturing);
+        launch_persistent(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->screen_lanes,
+                          c->lanes, c->pplan, c->stream);
+        rec(c, slot_ev(c, EV_FORCE_END), capturing);
+        if (nlaunch) *nlaunch += 2;
+        return;
+    }
     // candidate lists (when stale) and exact lists; in mixed precision the
     // density and equation of state too
     launch_tiles(st, c->s, c->tl, c->nleaves, c->multi, c->cap, fp64 ? 0 : 1, eos_of(c), c->met,
-                 out, c->stream, nlaunch);
+                 out, c->stream, nlaunch, c->screen_lanes);
     rec(c, slot_ev(c, EV_DENSITY), capturing);
     if (fp64) launch_density_fp64(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->stream);
     rec(c, slot_ev(c, EV_FORCE), capturing);
@@ -369,49 +392,119 @@ void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch, bool reso
     if (nlaunch) *nlaunch += 2;
 }
 
-// Autotuner: time the pair kernels with 4 and 8 threads per particle on the
-// bound state (after one neighbour search) and keep the faster.  The choice
-// depends on timing, so two contexts may sum pairs in different orders
-// (results agree to rounding); a fixed lanes_per_particle avoids that.
-sph_status autotune_lanes(sph_ctx *c)
+// Autotuner over the launch shape: threads per particle of the exact
+// screening (4 or 8) and of the pair kernels (4 or 8), and in mixed precision
+// whether the screening and force pass run as separate launches or as one
+// persistent launch.  After one right-hand side on the bound state, sph_init
+// times each variant of each stage (three launches after a warm-up one, CUDA
+// events on the context's stream) and keeps the faster; the lane counts of
+// the two stages are chosen independently (separate kernels), then the
+// persistent launch of the chosen lanes is timed against the two stages in
+// series.  The device counters are restored afterwards, so the tuning
+// launches are not counted.  The choice is cached for the process under the
+// configuration (device, n, stars, precision, capacity, metric, solids, what
+// is tuned and the fixed lanes), so later contexts of the same configuration
+// take the same shape without timing again.  Lane counts change the order of
+// the density and pair sums (a tuned context agrees with a fixed one to
+// rounding); the persistent launch does not change any result.
+using TuneKey = std::tuple<int, int64_t, int, int, int, int, int, int, int, int>;
+struct TuneVal {
+    int screen_lanes, lanes, persist;
+    int64_t ns[6];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+sph_status time_stage(sph_ctx *c, cudaEvent_t e0, cudaEvent_t e1, int64_t *ns,
+                      const std::function<void()> &launch)
 {
+    launch();
+    CUDA_TRY(cudaEventRecord(e0, c->stream));
+    for (int rep = 0; rep < 3; ++rep) launch();
+    CUDA_TRY(cudaEventRecord(e1, c->stream));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *ns = (int64_t)(ms * 1e6f / 3.f);
+    return SPH_OK;
+}
+
+sph_status autotune_shape(sph_ctx *c, bool lanes, bool persist)
+{
+    const bool fp64 = c->prec == SPH_FP64;
+    persist = persist && !fp64;
+    const int code = (lanes ? 1 : 0) | (persist ? 2 : 0) |
+                     (lanes ? 0 : 4 * (c->screen_lanes == 8 ? 1 : 0) + 8 * (c->lanes == 8 ? 1 : 0));
+    const TuneKey key{c->device, c->n, c->nstars, (int)c->prec, c->cap, c->met.kind,
+                      c->any_solid ? 1 : 0, c->multi, code, 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c->screen_lanes = it->second.screen_lanes;
+            c->lanes = it->second.lanes;
+            c->tune_persist = it->second.persist;
+            for (int k = 0; k < 6; ++k) c->tune_ns[k] = it->second.ns[k];
+            c->tuned = 2;
+            return SPH_OK;
+        }
+    }
+    DevScalars saved{};
+    CUDA_TRY(cudaMemcpy(&saved, c->s.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
     DevState st = state_of(c, c->P.vx, c->P.vy, c->P.vz, c->P.S);
-    int timing = c->timing;
+    const int timing = c->timing;
     c->timing = 0;
     enqueue_rhs(c, st, c->r, false, nullptr);
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    float best = 3e38f;
-    int best_lanes = 8;
-    const bool fp64 = c->prec == SPH_FP64;
-    for (int lanes : {4, 8}) {
-        c->lanes = lanes;
-        for (int rep = 0; rep < 4; ++rep) {
-            if (rep == 1) cudaEventRecord(e0, c->stream);
-            if (fp64)
-                launch_density_fp64(st, c->s, eos_of(c), c->met, c->r, c->cap, lanes, c->stream);
-            launch_force(st, c->s, eos_of(c), c->mat, c->met, c->r, c->cap, lanes, fp64, c->stream,
-                         c->side, c->ev_fork, c->ev_join);
+    sph_status rc = SPH_OK;
+    auto screen = [&](int sl) {
+        launch_screen(st, c->s, c->cap, fp64 ? 0 : 1, eos_of(c), c->met, c->r, c->stream, sl);
+    };
+    auto force = [&](int fl) {
+        if (fp64) launch_density_fp64(st, c->s, eos_of(c), c->met, c->r, c->cap, fl, c->stream);
+        launch_force(st, c->s, eos_of(c), c->mat, c->met, c->r, c->cap, fl, fp64, c->stream,
+                     c->side, c->ev_fork, c->ev_join);
+    };
+    const int shapes[2] = {4, 8};
+    if (lanes) {
+        for (int k = 0; k < 2 && rc == SPH_OK; ++k)
+            rc = time_stage(c, e0, e1, &c->tune_ns[k], [&] { screen(shapes[k]); });
+        for (int k = 0; k < 2 && rc == SPH_OK; ++k)
+            rc = time_stage(c, e0, e1, &c->tune_ns[2 + k], [&] { force(shapes[k]); });
+        if (rc == SPH_OK) {
+            c->screen_lanes = c->tune_ns[1] < c->tune_ns[0] ? 8 : 4;
+            c->lanes = c->tune_ns[3] < c->tune_ns[2] ? 8 : 4;
         }
-        cudaEventRecord(e1, c->stream);
-        float ms = 0.f;
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return fail(SPH_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
-        }
-        if (ms < best) {
-            best = ms;
-            best_lanes = lanes;
-        }
+    }
+    if (persist && rc == SPH_OK) {
+        const PersistPlan pp = plan_persistent(c->n, c->screen_lanes, c->lanes);
+        rc = time_stage(c, e0, e1, &c->tune_ns[4], [&] {
+            screen(c->screen_lanes);
+            force(c->lanes);
+        });
+        // the queue counters are reset per right-hand side by the bounding-box
+        // kernel; here before every timed launch
+        if (rc == SPH_OK)
+            rc = time_stage(c, e0, e1, &c->tune_ns[5], [&] {
+                cudaMemsetAsync(&c->s.sc->pq_head, 0, 2 * sizeof(unsigned int), c->stream);
+                launch_persistent(st, c->s, eos_of(c), c->mat, c->met, c->r, c->cap,
+                                  c->screen_lanes, c->lanes, pp, c->stream);
+            });
+        if (rc == SPH_OK) c->tune_persist = c->tune_ns[5] < c->tune_ns[4] ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->lanes = best_lanes;
     c->timing = timing;
+    if (rc != SPH_OK) return rc;
+    // the counters go back to their state before tuning
+    CUDA_TRY(cudaMemcpy(c->s.sc, &saved, sizeof(DevScalars), cudaMemcpyHostToDevice));
+    c->tuned = 1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneVal v{c->screen_lanes, c->lanes, c->tune_persist, {}};
+    for (int k = 0; k < 6; ++k) v.ns[k] = c->tune_ns[k];
+    g_tune_cache.emplace(key, v);
     return SPH_OK;
 }
 
@@ -530,6 +623,10 @@ sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_materi
         if (opt->lanes_per_particle != 0 && opt->lanes_per_particle != 4 &&
             opt->lanes_per_particle != 8 && opt->lanes_per_particle != -1)
             return fail(SPH_ERR_ARG, "lanes_per_particle must be -1, 0, 4 or 8");
+        if (opt->screen_lanes != 0 && opt->screen_lanes != 4 && opt->screen_lanes != 8)
+            return fail(SPH_ERR_ARG, "screen_lanes must be 0, 4 or 8");
+        if (opt->persistent < -1 || opt->persistent > 1)
+            return fail(SPH_ERR_ARG, "persistent must be -1, 0 or 1");
         if (opt->h_nmax < 0 || opt->h_nmin < 0 || (opt->h_nmax > 0 && opt->h_nmin > opt->h_nmax))
             return fail(SPH_ERR_ARG, "h_nmin/h_nmax band invalid");
         if (opt->sort_every < 0) return fail(SPH_ERR_ARG, "sort_every must be >= 0");
@@ -554,6 +651,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     }
     c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : kRowCap;
     c->lanes = c->opt.lanes_per_particle > 0 ? c->opt.lanes_per_particle : 8;
+    c->screen_lanes = c->opt.screen_lanes > 0 ? c->opt.screen_lanes : 4;
     c->stream = (cudaStream_t)stream;
     if (prec == SPH_MIXED) {
         CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
@@ -602,6 +700,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     while ((1 << sb) < c->nstars) ++sb;
     c->plan.key_bits_axis = bits_for(n);
     c->plan.star_bits = sb;
+    c->plan.nstars = c->nstars;
     c->multi = sb > 0 ? 1 : 0;
     int kb = 3 * c->plan.key_bits_axis + sb;
     c->plan.passes = (kb + 7) / 8;
@@ -645,6 +744,13 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     STATUS_TRY(c->alloc(&s.leaf_of, nn));
     STATUS_TRY(c->alloc(&s.bbox_partial, 6 * kBoxBlocksMax));
     STATUS_TRY(c->alloc(&s.bbox_done, 1));
+    s.star_box = nullptr;
+    if (c->nstars > 1) {
+        // per-star curve boxes: empty (lo at the top, hi at the bottom)
+        STATUS_TRY(c->alloc(&s.star_box, (size_t)6 * c->nstars));
+        CUDA_TRY(cudaMemset(s.star_box, 0xff, (size_t)3 * c->nstars * sizeof(uint32_t)));
+        CUDA_TRY(cudaMemset(s.star_box + 3 * c->nstars, 0, (size_t)3 * c->nstars * sizeof(uint32_t)));
+    }
     STATUS_TRY(c->alloc(&s.sc, 1));
     CUDA_TRY(cudaMemset(s.bbox_done, 0, sizeof(unsigned int)));
     CUDA_TRY(cudaMemset(s.sc, 0, sizeof(DevScalars)));
@@ -751,7 +857,13 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
                         cudaMemcpyHostToDevice));
     c->met.fstar = c->d_fstar;
     CUDA_TRY(cudaDeviceSynchronize());
-    if (c->opt.lanes_per_particle == -1 && n > 0) STATUS_TRY(autotune_lanes(c));
+    const bool tune_lanes = c->opt.lanes_per_particle == -1;
+    const bool tune_persist = c->opt.persistent == -1 && prec == SPH_MIXED;
+    if ((tune_lanes || tune_persist) && n > 0) STATUS_TRY(autotune_shape(c, tune_lanes, tune_persist));
+    if ((c->opt.persistent == 1 || (tune_persist && c->tune_persist)) && prec == SPH_MIXED && n > 0) {
+        c->pplan = plan_persistent(n, c->screen_lanes, c->lanes);
+        CUDA_TRY(cudaGetLastError());
+    }
     return SPH_OK;
 }
 
@@ -1033,13 +1145,13 @@ sph_status sph_totals_per_star(sph_ctx *c, double *out, int32_t nstars)
     return SPH_OK;
 }
 
-sph_status sph_stats(sph_ctx *c, int64_t out[24])
+sph_status sph_stats(sph_ctx *c, int64_t out[32])
 {
     if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
     DevScalars sc{};
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     CUDA_TRY(cudaMemcpy(&sc, c->s.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 24; ++k) out[k] = 0;
+    for (int k = 0; k < 32; ++k) out[k] = 0;
     out[0] = (int64_t)sc.pairs_last;
     out[1] = (int64_t)sc.pairs_total;
     out[2] = (int64_t)sc.rhs_count;
@@ -1059,6 +1171,12 @@ sph_status sph_stats(sph_ctx *c, int64_t out[24])
     out[16] = (int64_t)sc.tiles_last;
     out[17] = c->prec == SPH_FP64 ? 0 : 1;
     out[18] = (int64_t)sc.builds;
+    out[19] = c->screen_lanes;
+    out[20] = c->tuned;
+    for (int k = 0; k < 4; ++k) out[21 + k] = c->tune_ns[k];
+    out[25] = c->pplan.grid;
+    out[26] = c->tune_ns[4];
+    out[27] = c->tune_ns[5];
     return SPH_OK;
 }
 

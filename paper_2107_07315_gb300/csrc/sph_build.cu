@@ -28,13 +28,25 @@ __device__ __forceinline__ bool finite_bits(unsigned long long u)
     return ((u >> 52) & 0x7ffull) != 0x7ffull;
 }
 
+// Order-preserving integer image of a float's bits, and its inverse.
+__device__ __forceinline__ uint32_t enc_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float dec_f32(uint32_t e)
+{
+    return __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
+}
+
 // Bounding box of all positions.  Each block writes a partial; the last
 // block to finish reduces the partials, derives the position grid and
 // resets the per-RHS counters.  Also flags non-finite positions and h.
 // Minima and maxima are taken on order-preserving integer images of the
 // doubles, which keeps the scan off the (narrow) FP64 pipe.
 __global__ void k_bbox(DevState st, unsigned long long *partial, unsigned int *done,
-                       DevScalars *sc, uint32_t *radix_tot)
+                       DevScalars *sc, uint32_t *radix_tot, uint32_t *star_box, int nstars)
 {
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
@@ -87,8 +99,12 @@ __global__ void k_bbox(DevState st, unsigned long long *partial, unsigned int *d
     }
     __syncthreads();
     if (!last) return;
-    // the sort of this right-hand side starts from zero digit totals and tile counters
+    // the sort of this right-hand side starts from zero digit totals and tile
+    // counters, and (several stars) from empty per-star boxes
     for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) radix_tot[k] = 0u;
+    if (star_box)
+        for (int k = threadIdx.x; k < 6 * nstars; k += blockDim.x)
+            star_box[k] = k < 3 * nstars ? 0xffffffffu : 0u;
     if (threadIdx.x < 8) sc->tile_next[threadIdx.x] = 0u;
     // all threads of the last block reduce the block partials
     for (int k = 0; k < 3; ++k) {
@@ -152,6 +168,8 @@ __global__ void k_bbox(DevState st, unsigned long long *partial, unsigned int *d
         sc->growth_max = 0u;
         sc->resorted = 0;
         sc->xmax_f = (float)m * 1.000001f;
+        sc->pq_head = 0u;
+        sc->pq_done = 0u;
         sc->rhs_count += 1ull;
         *done = 0u;
     }
@@ -205,16 +223,41 @@ __device__ __forceinline__ uint32_t hilbert3(uint32_t x0, uint32_t x1, uint32_t 
 
 constexpr int kSortThreads = 256;
 constexpr int kMaxPasses = 8;
-constexpr int kSpinLimit = 1 << 22;  // default look-back polls before giving up (error flag)
 
-// Rounds of look-back reads a sort tile may make (DevScalars::spin_limit: 0
-// the default, > 0 that many, < 0 none: the first round gives up).
-__device__ __forceinline__ int spin_limit_of(const DevScalars *sc)
+// Bounding box of each star's fl32 positions (several stars, sort steps), so
+// that each star's curve key is taken over its own box: a star's curve order,
+// hence its leaves, then does not depend on where the other stars sit (over
+// the common box the curve leaves and re-enters a star's region, and leaves
+// of 8 consecutive particles at such jumps span much of the star).  Lanes of
+// a warp holding the same star reduce together (match, then min / max over
+// the group), one lane per star and warp updates the star's slots.
+// star_box: [6][nstars] encodings, lo x, y, z then hi x, y, z (reset by
+// k_bbox).
+__global__ void k_star_box(DevState st, uint32_t *star_box, int nstars)
 {
-    const int v = sc->spin_limit;
-    return v == 0 ? kSpinLimit : (v < 0 ? 0 : v);
+    const int64_t n = st.n;
+    const int lane = threadIdx.x & 31;
+    // the loop bound is block-uniform, so whole warps take part in every round
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool v = i < n;
+        const int s = v ? st.star[i] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, s);
+        const bool lead = v && lane == __ffs(grp) - 1;
+        const bool ok = v && s >= 0 && s < nstars;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double *X = k == 0 ? st.x : (k == 1 ? st.y : st.z);
+            const uint32_t e = v ? enc_f32(__double2float_rn(X[i])) : 0u;
+            const uint32_t mn = __reduce_min_sync(grp, v ? e : 0xffffffffu);
+            const uint32_t mx = __reduce_max_sync(grp, v ? e : 0u);
+            if (lead && ok) {
+                atomicMin(&star_box[k * nstars + s], mn);
+                atomicMax(&star_box[(3 + k) * nstars + s], mx);
+            }
+        }
+    }
 }
-
 
 // Space-filling-curve key of every particle (star id above the 3*bits bits of
 // the cell's Hilbert index), its identity value, and the digit histograms of
@@ -222,7 +265,8 @@ __device__ __forceinline__ int spin_limit_of(const DevScalars *sc)
 // Also clears the tile status words of all passes.
 __global__ void k_keys_hist(DevState st, DevScalars *sc, int bits, int passes,
                             unsigned long long *keys, uint32_t *vals, uint32_t *radix_tot,
-                            unsigned long long *status, int64_t status_words)
+                            unsigned long long *status, int64_t status_words,
+                            const uint32_t *star_box, int nstars)
 {
     __shared__ uint32_t h[kMaxPasses][256];
     for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0u;
@@ -240,14 +284,21 @@ __global__ void k_keys_hist(DevState st, DevScalars *sc, int bits, int passes,
          i += (int64_t)gridDim.x * blockDim.x) {
         const float p[3] = {__double2float_rn(st.x[i]), __double2float_rn(st.y[i]),
                             __double2float_rn(st.z[i])};
+        uint32_t s = st.star ? (uint32_t)st.star[i] : 0u;
         uint32_t q[3];
         for (int k = 0; k < 3; ++k) {
-            float t = (p[k] - lo[k]) * sc3[k];
+            float a = lo[k], b = sc3[k];
+            if (star_box && s < (uint32_t)nstars) {
+                // the star's own box (several stars)
+                a = dec_f32(star_box[k * nstars + s]);
+                const float ext = dec_f32(star_box[(3 + k) * nstars + s]) - a;
+                b = ext > 0.f ? cells / ext : 0.f;
+            }
+            float t = (p[k] - a) * b;
             t = fminf(fmaxf(t, 0.f), cells - 1.f);
             q[k] = (uint32_t)t;
         }
         unsigned long long key = (unsigned long long)hilbert3(q[0], q[1], q[2], bits);
-        uint32_t s = st.star ? (uint32_t)st.star[i] : 0u;
         key |= (unsigned long long)s << (3 * bits);
         keys[i] = key;
         vals[i] = (uint32_t)i;
@@ -621,8 +672,10 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
     int64_t nb = (n + kBoxThreads - 1) / kBoxThreads;
     int bblocks = (int)(nb < kBoxBlocksMax ? nb : kBoxBlocksMax);
     if (bblocks < 1) bblocks = 1;
+    const bool star_boxes = s.star_box && plan.nstars > 1 && st.star;
     k_bbox<<<bblocks, kBoxThreads, 0, stream>>>(
-        st, reinterpret_cast<unsigned long long *>(s.bbox_partial), s.bbox_done, s.sc, s.radix_tot);
+        st, reinterpret_cast<unsigned long long *>(s.bbox_partial), s.bbox_done, s.sc, s.radix_tot,
+        star_boxes ? s.star_box : nullptr, plan.nstars);
     ++nl;
     // the order of the last sort (every entry of perm is a valid caller index)
     const uint32_t *order = reinterpret_cast<const uint32_t *>(s.perm);
@@ -632,9 +685,14 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
         const int64_t status_words = (int64_t)plan.passes * plan.nblocks * 256;
         int kb = (int)((n + kSortThreads - 1) / kSortThreads);
         if (kb > 2 * kBoxBlocksMax) kb = 2 * kBoxBlocksMax;
+        if (star_boxes) {
+            k_star_box<<<kb, kSortThreads, 0, stream>>>(st, s.star_box, plan.nstars);
+            ++nl;
+        }
         k_keys_hist<<<kb, kSortThreads, 0, stream>>>(st, s.sc, plan.key_bits_axis, plan.passes,
                                                      s.keys[0], s.vals[0], s.radix_tot, status,
-                                                     status_words);
+                                                     status_words, star_boxes ? s.star_box : nullptr,
+                                                     plan.nstars);
         ++nl;
         for (int p = 0; p < plan.passes; ++p) {
             int src = p & 1, dst = src ^ 1;

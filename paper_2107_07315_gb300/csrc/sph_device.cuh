@@ -383,6 +383,16 @@ __device__ __forceinline__ bool order_invalid(const DevScalars *sc)
     return (*(volatile const int *)&sc->err & ERR_TIMEOUT) != 0;
 }
 
+constexpr int kSpinLimit = 1 << 22;  // default polls of a device-side wait before giving up
+
+// Polls a device-side wait may make (DevScalars::spin_limit: 0 the default,
+// > 0 that many, < 0 none: the first poll gives up).
+__device__ __forceinline__ int spin_limit_of(const DevScalars *sc)
+{
+    const int v = sc->spin_limit;
+    return v == 0 ? kSpinLimit : (v < 0 ? 0 : v);
+}
+
 // Particle range [first, end) of leaf l: leaves of one star hold 8
 // consecutive sorted particles; several stars read the leaf table.
 template <bool MULTI_STAR>

@@ -29,6 +29,9 @@
 //   nbr[n*cap]   : exact neighbour list of each sorted particle (ascending),
 //                  ncnt[n] its length; screened from vlist every right-hand
 //                  side.
+//   star_box[6][nstars] : several stars only: each star's fl32 bounding box
+//                  (order-preserving integer images, lo x y z then hi x y z);
+//                  the curve keys of a star are taken over its own box.
 #pragma once
 
 #include <cstdint>
@@ -88,6 +91,9 @@ struct DevScalars {
     int rebuild;                     // this RHS rebuilds the candidate lists
     float xmax_f;                    // largest |coordinate| (for the displacement bound)
     unsigned long long builds;       // candidate-list builds so far
+    // work queue of the persistent right-hand-side kernel (reset per RHS)
+    unsigned int pq_head;            // next item to dequeue
+    unsigned int pq_done;            // screening items completed
 };
 
 struct DevState {
@@ -225,6 +231,7 @@ struct Scratch {
     int32_t *leaf_of;         // [n] leaf of each sorted slot
     double *bbox_partial;     // [6 * 304]
     unsigned int *bbox_done;  // block counter of the bounding-box kernel
+    uint32_t *star_box;       // [6][nstars] per-star fl32 box (several stars; else null)
     DevScalars *sc;
 };
 
@@ -232,6 +239,7 @@ struct Scratch {
 struct SortPlan {
     int key_bits_axis;  // cell bits per axis of the curve key
     int star_bits;
+    int nstars;         // stars in the index space (per-star curve boxes when > 1)
     int passes;         // 8-bit digit passes
     int ipt;            // items per thread in sort kernels
     int nblocks;        // sort tiles
@@ -255,7 +263,35 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
 // cap: list capacity per particle (SPH_ERR_CAPACITY above it).
 void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
                   int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
-                  const DevRates &out, cudaStream_t stream, int *nlaunch = nullptr);
+                  const DevRates &out, cudaStream_t stream, int *nlaunch = nullptr,
+                  int screen_lanes = 4);
+
+// Exact screening (with the density and equation of state when density is
+// true) alone, from the candidate lists of the last build; the autotuner
+// times it.
+void launch_screen(const DevState &st, const Scratch &s, int cap, int density,
+                   const DevEos &eos, const DevMetric &g, const DevRates &out,
+                   cudaStream_t stream, int screen_lanes);
+
+// Candidate-list build alone (the kernel returns at once unless the tree
+// kernel asked for a rebuild).
+void launch_tiles_build(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
+                        int multi_star, int cap, cudaStream_t stream);
+
+// Persistent right-hand side, mixed precision (one launch): grid blocks
+// dequeue items from a global counter; items 0 .. nA-1 screen a block of
+// particles (exact lists, density, equation of state), the rest run the
+// force pass of a block of particles once every screening item is done.
+// screen_lanes / lanes: threads per particle of the two item kinds.
+struct PersistPlan {
+    int grid = 0;          // resident blocks (SMs x blocks per SM)
+    int n_screen = 0;      // screening items
+    int n_force = 0;       // force items
+};
+PersistPlan plan_persistent(int64_t n, int screen_lanes, int lanes);
+void launch_persistent(const DevState &st, const Scratch &s, const DevEos &eos,
+                       const DevMaterial &mat, const DevMetric &g, const DevRates &out, int cap,
+                       int screen_lanes, int lanes, const PersistPlan &pp, cudaStream_t stream);
 
 // FP64 density summation and equation of state over the neighbour lists.
 void launch_density_fp64(const DevState &st, const Scratch &s, const DevEos &eos,

@@ -175,6 +175,7 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
     SortPlan plan{};
     plan.key_bits_axis = bits_for_n(n);
     plan.star_bits = 0;
+    plan.nstars = 1;
     plan.passes = (3 * plan.key_bits_axis + 7) / 8;
     plan.ipt = 1;
     plan.nblocks = (int)((n + 255) / 256);
@@ -230,7 +231,7 @@ extern "C" sph_status sph_neighbors_noalloc(int64_t n, const double *x, const do
     if (err & ERR_CAPACITY)
         return fail(SPH_ERR_CAPACITY,
                     "sph_neighbors_noalloc: a particle has more than 128 neighbours, or a leaf "
-                    "more than 512 candidate leaves");
+                    "more than 256 candidate leaves");
     if (err & ERR_BOUNDS) return fail(SPH_ERR_BOUNDS, "sph_neighbors_noalloc: index out of bounds");
     if (tot > cap) return fail(SPH_ERR_CAPACITY, "sph_neighbors_noalloc: lists exceed cap");
     launch_export_fill(s, n, kCap, offsets, idx, stream);

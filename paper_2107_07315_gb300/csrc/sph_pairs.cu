@@ -19,7 +19,9 @@
 // (exact Xhi differences plus FP32 remainders), a compensated (Kahan) sum for
 // du/dt, per-particle terms in FP32 with integer-emulated conversions to and
 // from the FP64 state (no FP64 instruction in the mixed force kernels).
-#include "sph_device.cuh"
+#include <algorithm>
+
+#include "sph_screen.cuh"
 
 namespace sph {
 
@@ -125,22 +127,30 @@ enum { A_P0, A_P1, A_P2, A_X0, A_X1, A_X2, A_DU, A_DUC, A_DD, A_G00, A_G01, A_G0
 // live registers, 8 blocks of 128 threads per SM), SOLID = true the blocks
 // holding a solid particle (6 blocks per SM: at most 85 registers, which
 // keeps the allocation at 80).  Each returns at once on the other's blocks.
-template <int LPI, int R, bool SOLID>
-__global__ void __launch_bounds__(kTB, SOLID ? 6 : 8)
-k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
-              DevRates out, int cap)
+//
+// force_block runs block blk (PB = kTB / LPI * R consecutive sorted
+// particles); every thread of the block calls it (one block barrier inside).
+template <int LPI, int R>
+__host__ __device__ constexpr int force_pb() { return kTB / LPI * R; }
+
+// 1 when block blk of PB particles holds a solid particle (a block barrier).
+template <int PB>
+__device__ __forceinline__ bool block_has_solid(const Scratch &s, int64_t n, int64_t blk)
 {
-    (void)eos;
-    constexpr int PB = kTB / LPI * R;
-    __shared__ float s_acc[A_N][PB];
+    const int64_t ib = blk * PB + threadIdx.x;
+    const bool mine = threadIdx.x < PB && ib < n && s.tys[ib] == 1;
+    return __syncthreads_or(mine) != 0;
+}
+
+template <int LPI, int R, bool SOLID>
+__device__ __forceinline__ void force_block(int64_t n, const DevState &st, const Scratch &s,
+                                            const DevMaterial &mat, const DevMetric &g,
+                                            const DevRates &out, int cap, int64_t blk,
+                                            float (*s_acc)[force_pb<LPI, R>()])
+{
+    constexpr int PB = force_pb<LPI, R>();
     const int grp = threadIdx.x / LPI, sub = threadIdx.x % LPI;
-    const int64_t base = (int64_t)blockIdx.x * PB;
-    if (order_invalid(s.sc)) return;  // uniform across the grid
-    {
-        const int64_t ib = base + threadIdx.x;
-        const bool mine = threadIdx.x < PB && ib < n && s.tys[ib] == 1;
-        if ((__syncthreads_or(mine) != 0) != SOLID) return;
-    }
+    const int64_t base = blk * PB;
     const float alpha_av = mat.alpha_f, beta_av = mat.beta_f, eta2 = mat.eta2_f;
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
@@ -260,6 +270,19 @@ k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, De
     finalize<float>(c, st.n, st, mat, g, star, solid_i, a2.w, aP, aX,
                     s_acc[A_DU][t] - s_acc[A_DUC][t], s_acc[A_DD][t], G, p0.x, p0.z, p0.w, p1.x,
                     a2.x, a2.y, a2.z, pos, out);
+}
+
+template <int LPI, int R, bool SOLID>
+__global__ void __launch_bounds__(kTB, SOLID ? 6 : 8)
+k_force_mixed(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
+              DevRates out, int cap)
+{
+    (void)eos;
+    constexpr int PB = force_pb<LPI, R>();
+    __shared__ float s_acc[A_N][PB];
+    if (order_invalid(s.sc)) return;  // uniform across the grid
+    if (block_has_solid<PB>(s, n, blockIdx.x) != SOLID) return;
+    force_block<LPI, R, SOLID>(n, st, s, mat, g, out, cap, blockIdx.x, s_acc);
 }
 
 template <int LPI, int R>
@@ -383,6 +406,75 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
                      s_acc[A_DD][t], G, pp[0], pp[2], pp[3], pp[4], a1.y, a1.z, a1.w, pos, out);
 }
 
+// ------------------------------------------------------- persistent RHS
+// One launch for the exact screening (with the density and equation of
+// state) and the force pass of all particles, of one star or of a batch of
+// stars in one index space.  Every block loops: it takes the next item from
+// the global counter sc->pq_head; items 0 .. nA-1 screen block `item` of
+// 128 / LS particles, items nA .. nA+nB-1 run the force pass of block
+// item - nA of force_pb<LF, kRoundsF>() particles (stars are contiguous in
+// the sorted order, so one star's blocks are consecutive items).
+//
+// Dependency: a force item reads the density, pressure and stress of every
+// neighbour, written by screening items.  A block finishing a screening item
+// publishes it (block barrier, device fence, counter sc->pq_done); a force
+// item first waits until pq_done == nA.  Every screening item precedes every
+// force item in the queue, so when a force item is dequeued every screening
+// item has been taken by a running block, and screening items never wait:
+// the count always completes, whether or not all blocks are resident.  The
+// wait still polls at most spin_limit_of(sc) times (ERR_TIMEOUT, after which
+// every force item returns at once; the host reports SPH_ERR_TIMEOUT).
+template <int LS, int LF>
+__global__ void __launch_bounds__(kTB, 6)
+k_rhs_persistent(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, DevMetric g,
+                 DevRates out, int cap, int n_screen, int n_force)
+{
+    constexpr int PB = force_pb<LF, kRoundsF>();
+    __shared__ float s_acc[A_N][PB];
+    __shared__ int s_item, s_ok;
+    DevScalars *sc = s.sc;
+    if (order_invalid(sc)) return;  // uniform: set before this launch
+    const int total = n_screen + n_force;
+    for (;;) {
+        __syncthreads();  // the last item is done with s_acc and s_item
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&sc->pq_head, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) return;
+        if (item < n_screen) {
+            screen_block<true, LS>(st, s, cap, eos, g, out, (int64_t)item);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&sc->pq_done, 1u);
+            }
+            continue;
+        }
+        if (threadIdx.x == 0) {
+            const int limit = spin_limit_of(sc);
+            int polls = 0, ok = 1;
+            while (*(volatile unsigned int *)&sc->pq_done < (unsigned int)n_screen) {
+                if (order_invalid(sc) || polls >= limit) {
+                    ok = 0;
+                    break;
+                }
+                ++polls;
+                __nanosleep(128);
+            }
+            if (!ok) atomicOr(&sc->err, ERR_TIMEOUT);
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;  // uniform across the block
+        const int64_t blk = item - n_screen;
+        if (block_has_solid<PB>(s, n, blk))
+            force_block<LF, kRoundsF, true>(n, st, s, mat, g, out, cap, blk, s_acc);
+        else
+            force_block<LF, kRoundsF, false>(n, st, s, mat, g, out, cap, blk, s_acc);
+    }
+}
+
 }  // namespace
 
 // Particles per block of each kernel variant (threads / lanes * rounds).
@@ -441,6 +533,58 @@ void launch_force(const DevState &st, const Scratch &s, const DevEos &eos, const
     if (fan) {
         cudaEventRecord(join, side);
         cudaStreamWaitEvent(stream, join, 0);
+    }
+}
+
+template <int LS, int LF>
+static void *persistent_fn()
+{
+    return (void *)k_rhs_persistent<LS, LF>;
+}
+
+static void *persistent_kernel(int screen_lanes, int lanes)
+{
+    if (screen_lanes == 8) return lanes == 4 ? persistent_fn<8, 4>() : persistent_fn<8, 8>();
+    return lanes == 4 ? persistent_fn<4, 4>() : persistent_fn<4, 8>();
+}
+
+PersistPlan plan_persistent(int64_t n, int screen_lanes, int lanes)
+{
+    PersistPlan p;
+    const int ps = kScreenThreads / (screen_lanes == 8 ? 8 : 4);
+    const int pf = lanes == 4 ? force_pb<4, kRoundsF>() : force_pb<8, kRoundsF>();
+    p.n_screen = (int)((n + ps - 1) / ps);
+    p.n_force = (int)((n + pf - 1) / pf);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_kernel(screen_lanes, lanes),
+                                                  kTB, 0);
+    p.grid = std::max(1, sms * std::max(per, 1));
+    return p;
+}
+
+void launch_persistent(const DevState &st, const Scratch &s, const DevEos &eos,
+                       const DevMaterial &mat, const DevMetric &g, const DevRates &out, int cap,
+                       int screen_lanes, int lanes, const PersistPlan &pp, cudaStream_t stream)
+{
+    const int64_t n = st.n;
+    if (n == 0) return;
+    const int grid = std::min(pp.grid, pp.n_screen + pp.n_force);
+    if (screen_lanes == 8) {
+        if (lanes == 4)
+            k_rhs_persistent<8, 4><<<grid, kTB, 0, stream>>>(n, st, s, eos, mat, g, out, cap,
+                                                             pp.n_screen, pp.n_force);
+        else
+            k_rhs_persistent<8, 8><<<grid, kTB, 0, stream>>>(n, st, s, eos, mat, g, out, cap,
+                                                             pp.n_screen, pp.n_force);
+    } else {
+        if (lanes == 4)
+            k_rhs_persistent<4, 4><<<grid, kTB, 0, stream>>>(n, st, s, eos, mat, g, out, cap,
+                                                             pp.n_screen, pp.n_force);
+        else
+            k_rhs_persistent<4, 8><<<grid, kTB, 0, stream>>>(n, st, s, eos, mat, g, out, cap,
+                                                             pp.n_screen, pp.n_force);
     }
 }
 

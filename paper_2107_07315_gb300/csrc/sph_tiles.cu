@@ -62,7 +62,7 @@
 // and the band takes 48 u (g + e) hs for its absolute part.  Outside a band
 // the FP32 sign is the exact sign; inside it the FP64 predicate decides (exact
 // lists) or the pair is kept (candidate lists).
-#include "sph_device.cuh"
+#include "sph_screen.cuh"
 
 namespace sph {
 
@@ -71,18 +71,6 @@ namespace {
 constexpr int kTileWarps = 4;
 constexpr int kTileThreads = 32 * kTileWarps;
 constexpr int kChunk = 4;  // candidate leaves staged per chunk (32 particles)
-constexpr float kBandRel = 2e-6f;
-
-// Exact FP64 predicate in the oracle's operation order (no contraction).
-__device__ __forceinline__ bool pair_in_fp64(double xa, double ya, double za, double ha,
-                                             double xb, double yb, double zb, double hb)
-{
-    double dx = __dsub_rn(xa, xb), dy = __dsub_rn(ya, yb), dz = __dsub_rn(za, zb);
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    double hsum = __dadd_rn(ha, hb);
-    return r2 < __dmul_rn(hsum, hsum);
-}
-
 template <bool MULTI_STAR>
 __global__ void __launch_bounds__(kTileThreads, 8)
 k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
@@ -324,180 +312,54 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
         s.pos_build[i] = p;  // the positions and h these lists hold for
         atomicMin((unsigned *)&sc->hmin_build, __float_as_uint(p.w));
     }
-    if (lane == 0) {
-        atomicMax(&sc->max_cand, nc);
-        atomicAdd(&sc->tiles_last, (unsigned long long)nc);
-    }
     if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&sc->err, ERR_CAPACITY);
 }
 
-// Exact lists from the candidate lists, every right-hand side: LPI = 4 lanes
-// per particle, 32 particles per block.  With DENSITY (mixed precision) also
-// the density summation and the equation of state.  The exact list of a
-// particle is a subsequence of its candidate list, so the two may share
-// memory: every entry is written at or before the last one read.
-constexpr int kScreenThreads = 128;
-template <bool DENSITY>
+// Exact lists from the candidate lists, every right-hand side (with the
+// density and equation of state when DENSITY): one block of particles per
+// CUDA block.
+template <bool DENSITY, int LPI>
 __global__ void __launch_bounds__(kScreenThreads, 8)
 k_screen(DevState st, Scratch s, int cap, DevEos eos, DevMetric g, DevRates out)
 {
     if (order_invalid(s.sc)) return;  // uniform across the grid
-    const int64_t n = st.n;
-    const int lane = threadIdx.x & 31, sub = lane & 3;
-    const int64_t i0 = (int64_t)blockIdx.x * (kScreenThreads / 4) + (threadIdx.x >> 2);
-    const bool valid = i0 < n;
-    const int64_t i = valid ? i0 : 0;
-    DevScalars *sc = s.sc;
-    const float band_abs = sc->band_abs;
-    const float4 a0 = s.rec[i], a1 = s.rec[n + i];
-    const int vc = valid ? s.vcnt[i] : 0;
-    const int32_t *vl = s.vlist + i * cap;
-    int32_t *nl = s.nbr + i * cap;
-    const unsigned gshift = lane & ~3u;
-    int pos = 0;
-    unsigned long long nre = 0;
-    float sum = 0.f, comp = 0.f;
-    // every lane runs to the warp's longest list: the ballot and shuffle below
-    // need the whole warp (a lane past its own list tests an old, valid j and
-    // drops it).  The records of the next candidate are loaded one iteration
-    // ahead, its index two ahead, so two gathers per lane are in flight.
-    const int vmax = __reduce_max_sync(0xffffffffu, vc);
-    int jn = sub < vc ? vl[sub] : 0;
-    float4 n0 = s.rec[jn], n1 = s.rec[n + jn];
-    int jnn = sub + 4 < vc ? vl[sub + 4] : 0;
-    for (int k0 = 0; k0 < vmax; k0 += 4) {
-        const int k = k0 + sub;
-        const bool kv = k < vc;
-        const int j = jn;
-        const float4 b0 = n0, b1 = n1;
-        jn = jnn;
-        if (k + 4 < vc) {
-            n0 = s.rec[jn];
-            n1 = s.rec[n + jn];
-        }
-        jnn = k + 8 < vc ? vl[k + 8] : 0;
-        const float dx = (a0.x - b0.x) + (a1.x - b1.x);
-        const float dy = (a0.y - b0.y) + (a1.y - b1.y);
-        const float dz = (a0.z - b0.z) + (a1.z - b1.z);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float hs = a0.w + b0.w;
-        const float hs2 = hs * hs;
-        const float d = r2 - hs2;
-        const float M = fmaf(kBandRel, r2 + hs2, band_abs * hs);
-        bool in = d < -M;
-        if (kv && fabsf(d) <= M) {
-            ++nre;
-            in = pair_in_fp64(s.xs[i], s.ys[i], s.zs[i], s.hs[i], s.xs[j], s.ys[j], s.zs[j],
-                              s.hs[j]);
-        }
-        in = in && kv;
-        const unsigned bits = (__ballot_sync(0xffffffffu, in) >> gshift) & 0xfu;
-        const int nh = __popc(bits);
-        if (in) nl[pos + __popc(bits & ((1u << sub) - 1u))] = j;
-        if (DENSITY) {
-            // m_b W(r_ab, h_ab) of this lane's candidate (used if it is a hit)
-            const float r = r2 * rsqrtf(fmaxf(r2, 1.17549435e-38f));
-            const float hinv = __fdividef(2.f, hs);  // 1/h_ab
-            const float qq = r * hinv;
-            const float sig = hinv * hinv * hinv * kInvPiF;
-            const float t = 2.f - qq;
-            const float W = qq < 1.f ? sig * fmaf(qq * qq, fmaf(0.75f, qq, -1.5f), 1.f)
-                                     : sig * 0.25f * t * t * t;
-            const float term = b1.w * W;
-            // lane sub sums the hits whose rank in the exact list is sub mod 4,
-            // in rank order: the same sums as a pass over the exact list, so
-            // the density does not depend on which candidate list held them.
-            // This round's hits hold ranks pos .. pos + nh - 1; the one of rank
-            // = sub (mod 4) is hit number idx, on lane src of the group.
-            const int idx = (sub - pos) & 3;
-            int src = sub, c = 0;
-#pragma unroll
-            for (int bq = 0; bq < 4; ++bq) {
-                if ((bits >> bq) & 1u) {
-                    if (c == idx) src = bq;
-                    ++c;
-                }
-            }
-            const float tv = __shfl_sync(0xffffffffu, term, (int)gshift + src);
-            if (idx < nh) {
-                const float y = tv - comp;
-                const float tt = sum + y;
-                comp = (tt - sum) - y;
-                sum = tt;
-            }
-        }
-        pos += nh;
-    }
-    if (DENSITY) {
-        for (int o = 1; o < 4; o <<= 1) {
-            sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            comp += __shfl_xor_sync(0xffffffffu, comp, o);
-        }
-    }
-    const bool lead = valid && sub == 0;
-    if (lead) s.ncnt[i] = pos;
-    unsigned long long pairs = lead ? (unsigned long long)pos : 0ull;
-    int cmax = lead ? pos : 0;
-    for (int o = 16; o > 0; o >>= 1) {
-        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-        nre += __shfl_xor_sync(0xffffffffu, nre, o);
-        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-    }
-    if (lane == 0) {
-        atomicAdd(&sc->pairs_last, pairs);
-        atomicAdd(&sc->pairs_total, pairs);
-        if (nre) atomicAdd(&sc->rechecks, nre);
-        atomicMax(&sc->max_count, cmax);
-    }
-    if (!DENSITY || !lead) return;
-
-    // equation of state of particle i
-    const float hi = a0.w;
-    const float D = a1.w * kInvPiF / (hi * hi * hi) + (sum - comp);
-    const int c = s.perm[i];
-    const int star = st.star ? st.star[c] : 0;
-    const float vx = f64_to_f32_rn(st.vx[c]), vy = f64_to_f32_rn(st.vy[c]),
-                vz = f64_to_f32_rn(st.vz[c]);
-    const PosF posf{a0.x, a0.y, a0.z, a1.x, a1.y, a1.z};
-    Prep<float> pr = eos_prep<float>(eos, g, star, D, vx, vy, vz, posf);
-    const float invD = 1.f / D;
-    const float PD2 = pr.P * invD * invD;
-    const bool solid = s.tys[i] == 1;
-    s.rec[2 * n + i] = make_float4(vx, vy, vz, D);
-    s.rec[3 * n + i] = make_float4(PD2, pr.cs, invD, solid ? 1.f : 0.f);
-    if (solid) {
-        const int64_t N = st.n;
-        const float f = invD * invD;
-        s.sd2[i] = make_float4(f64_to_f32_rn(st.S[c]) * f, f64_to_f32_rn(st.S[N + c]) * f,
-                               f64_to_f32_rn(st.S[2 * N + c]) * f, f64_to_f32_rn(st.S[3 * N + c]) * f);
-        s.sd2[n + i] = make_float4(f64_to_f32_rn(st.S[4 * N + c]) * f,
-                                   f64_to_f32_rn(st.S[5 * N + c]) * f, 0.f, 0.f);
-    } else {
-        s.sd2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s.sd2[n + i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    s.pp[i * 2 + 0] = make_float4(pr.rho, pr.P, pr.cP, pr.henth);
-    s.pp[i * 2 + 1] = make_float4(pr.Wt, pr.cs, D, 0.f);
-    out.D[c] = to_out(D);
-    out.rho[c] = to_out(pr.rho);
-    out.P[c] = to_out(pr.P);
-    out.cs[c] = to_out(pr.cs);
-    out.ncount[c] = pos;
+    screen_block<DENSITY, LPI>(st, s, cap, eos, g, out, (int64_t)blockIdx.x);
 }
 
 }  // namespace
 
-void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
-                  int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
-                  const DevRates &out, cudaStream_t stream, int *nlaunch)
+void launch_screen(const DevState &st, const Scratch &s, int cap, int density,
+                   const DevEos &eos, const DevMetric &g, const DevRates &out,
+                   cudaStream_t stream, int screen_lanes)
+{
+    if (st.n <= 0) return;
+    if (screen_lanes == 8) {
+        const int ns = (int)((st.n + kScreenThreads / 8 - 1) / (kScreenThreads / 8));
+        if (density) k_screen<true, 8><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
+        else k_screen<false, 8><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
+    } else {
+        const int ns = (int)((st.n + kScreenThreads / 4 - 1) / (kScreenThreads / 4));
+        if (density) k_screen<true, 4><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
+        else k_screen<false, 4><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
+    }
+}
+
+void launch_tiles_build(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
+                        int multi_star, int cap, cudaStream_t stream)
 {
     if (nleaves <= 0) return;
     const int nb = (nleaves + kTileWarps - 1) / kTileWarps;
     if (multi_star) k_tiles<true><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap);
     else k_tiles<false><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap);
-    const int ns = (int)((st.n + kScreenThreads / 4 - 1) / (kScreenThreads / 4));
-    if (density) k_screen<true><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
-    else k_screen<false><<<ns, kScreenThreads, 0, stream>>>(st, s, cap, eos, g, out);
+}
+
+void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
+                  int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
+                  const DevRates &out, cudaStream_t stream, int *nlaunch, int screen_lanes)
+{
+    if (nleaves <= 0) return;
+    launch_tiles_build(st, s, tl, nleaves, multi_star, cap, stream);
+    launch_screen(st, s, cap, density, eos, g, out, stream, screen_lanes);
     if (nlaunch) *nlaunch += 2;
 }
 

@@ -94,7 +94,8 @@ class sph_rates(C.Structure):
 class sph_options(C.Structure):
     _fields_ = [("h_nmin", C.c_int32), ("h_nmax", C.c_int32), ("max_neighbors", C.c_int32),
                 ("lanes_per_particle", C.c_int32), ("use_graph", C.c_int32),
-                ("totals_every", C.c_int32), ("sort_every", C.c_int32), ("skin", C.c_double)]
+                ("totals_every", C.c_int32), ("sort_every", C.c_int32), ("skin", C.c_double),
+                ("screen_lanes", C.c_int32), ("persistent", C.c_int32)]
 
 
 _lib = None
@@ -293,7 +294,8 @@ def sph_init(particles: dict, eos: dict, material: dict, metric=None, precision=
                         int(options.get("max_neighbors", 0)),
                         int(options.get("lanes_per_particle", 0)), int(options.get("use_graph", 1)),
                         int(options.get("totals_every", 0)), int(options.get("sort_every", 0)),
-                        float(options.get("skin", 0.0)))
+                        float(options.get("skin", 0.0)), int(options.get("screen_lanes", 0)),
+                        int(options.get("persistent", 0)))
     if stream is None:
         import torch
 
@@ -368,7 +370,7 @@ def sph_totals_per_star(ctx: SphCtx, nstars: int) -> np.ndarray:
 
 
 def sph_stats(ctx: SphCtx) -> np.ndarray:
-    out = np.zeros(24, np.int64)
+    out = np.zeros(32, np.int64)
     _check(lib().sph_stats(ctx.handle, out.ctypes.data_as(_i64)), "sph_stats")
     return out
 

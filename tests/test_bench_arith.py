@@ -41,3 +41,37 @@ def test_roofline_entries():
     assert r64["all"]["force"]["frac"] > al["force"]["frac"] * 10
     rhs = b._rhs_only(tim, pairs)
     assert rhs["ms"] == pytest.approx(0.15 + 0.0 + 0.06)
+
+
+def test_launch_shape_record():
+    b = _bench()
+    st = [0] * 32
+    st[7], st[19], st[20] = 4, 8, 1
+    st[21:25] = [50000, 40000, 30000, 45000]  # ns: screen 4/8, pairs 4/8
+    sh = b.launch_shape(st)
+    assert sh["screen_lanes"] == 8 and sh["pair_lanes"] == 4 and sh["source"] == "autotuned"
+    assert sh["tuner_us_per_launch"]["screen_8"] == pytest.approx(40.0)
+    # fixed default (screen 4, pairs 8) against the chosen (screen 8, pairs 4)
+    assert sh["tuned_vs_fixed"] == pytest.approx((50000 + 45000) / (40000 + 30000))
+    st[20], st[21:25] = 0, [0, 0, 0, 0]
+    sh = b.launch_shape(st)
+    assert sh["source"] == "fixed" and "tuned_vs_fixed" not in sh
+
+
+def test_profile_traffic_follows_source_hash(tmp_path, monkeypatch):
+    # traffic is read from a summary only while its kernel sources are unchanged
+    b = _bench()
+    h = b.source_hash(("sph_tiles.cu", "sph_screen.cuh", "sph_device.cuh"))
+    assert len(h) == 16
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    for name, t in (("tiles_star1e5.md", 100), ("screen_star1e5.md", 50)):
+        (prof / name).write_text("kernel_source_sha256_16: %s\ndram_bytes_per_launch: %d\n" % (h, t))
+    csrc = os.path.join(ROOT, "paper_2107_07315_gb300", "csrc")
+    (tmp_path / "paper_2107_07315_gb300").mkdir()
+    os.symlink(csrc, tmp_path / "paper_2107_07315_gb300" / "csrc")
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.traffic_from_profile("lists") == 150.0
+    (prof / "screen_star1e5.md").write_text("kernel_source_sha256_16: 0000000000000000\n"
+                                            "dram_bytes_per_launch: 50\n")
+    assert b.traffic_from_profile("lists") is None

@@ -218,13 +218,28 @@ def test_crust_failure_flags():
     assert not np.any(diff & ~m32) or diff.sum() <= 3
 
 
-def test_autotuned_lanes_match():
-    st, eos = I.random_state(3000, seed=51, vel=0.2, stress=0.05)
+def test_autotuned_shape_matches_and_is_cached():
+    # n = 3001 is used by no other test, so the first context times the
+    # shapes and the second takes them from the process cache
+    st, eos = I.random_state(3001, seed=51, vel=0.2, stress=0.05)
     o = oracle.rhs(st, eos, MAT, None, scales=True)
     g, ctx, _ = gpu_rhs(st, eos, MAT, None, sph.SPH_MIXED, dict(lanes_per_particle=-1))
     stats = sph.sph_stats(ctx)
-    assert stats[7] in (4, 8)
+    assert stats[7] in (4, 8) and stats[19] in (4, 8)
+    assert stats[20] == 1 and np.all(stats[21:25] > 0)
+    # the faster of each pair was kept
+    assert stats[19] == (8 if stats[22] < stats[21] else 4)
+    assert stats[7] == (8 if stats[24] < stats[23] else 4)
+    # the tuning launches are not counted: one right-hand side, one build
+    assert stats[2] == 1 and stats[18] == 1
     assert_close(g, o, TOL_MIXED, label="autotune")
+    g2, ctx2, _ = gpu_rhs(st, eos, MAT, None, sph.SPH_MIXED, dict(lanes_per_particle=-1))
+    s2 = sph.sph_stats(ctx2)
+    assert s2[20] == 2 and s2[7] == stats[7] and s2[19] == stats[19]
+    assert np.array_equal(s2[21:25], stats[21:25])
+    # same shape, same order of sums: the same rates bit for bit
+    for k in ("ax", "ay", "az", "dudt", "D"):
+        assert np.array_equal(g[k], g2[k]), k
 
 
 def _quadrupole_series(st, eos, met, prec, dt, nsteps, every):

@@ -5,6 +5,9 @@
   raises the timeout.  sph_sync reports SPH_ERR_TIMEOUT, no kernel consumes
   the invalid order, and after the default limit is restored the same
   context computes the oracle's right-hand side again.
+* The same for the persistent launch: a step without a curve sort whose force
+  items may not wait for the screening items reports the timeout, and the
+  context then evaluates its current state as the oracle does.
 * A checkpoint whose stored particle order points outside the particle range
   is refused on the host with SPH_ERR_BOUNDS before anything is copied; one
   with a repeated entry with SPH_ERR_ARG.
@@ -106,4 +109,38 @@ def test_checkpoint_order_outside_range_is_a_bounds_error():
         assert np.array_equal(before[k], after[k])
     sph.sph_step(ctx, 1e-3, 1)
     sph.sph_sync(ctx)
+    sph.sph_free(ctx)
+
+
+def test_persistent_queue_wait_timeout_is_reported():
+    # a step without a curve sort, so the only wait is the force items' wait
+    # for the screening items of the persistent launch: with no polls allowed
+    # the force items that start before the screening is done give up (the
+    # 3000 particles make about 190 items, fewer than the resident blocks, so
+    # every item starts at once)
+    st, eos = I.random_state(3000, seed=63, vel=0.1, stress=0.05)
+    n = len(st["x"])
+    dev = sph.device_state(st)
+    torch.cuda.synchronize()
+    ctx = sph.sph_init(dev, eos, MAT, None, sph.SPH_MIXED, dict(persistent=1, sort_every=1000),
+                       stream=stream().cuda_stream)
+    assert sph.sph_stats(ctx)[25] > 0
+    dt = 0.5 * I.cfl_dt(st, eos)
+    sph.sph_step(ctx, dt, 1)
+    sph.sph_sync(ctx)
+    sph.sph_set_wait_limit(ctx, 0)
+    sph.sph_step(ctx, dt, 1)
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_sync(ctx)
+    assert e.value.status == 5, e.value
+    # default limit again: the context evaluates the current state correctly
+    sph.sph_set_wait_limit(ctx, -1)
+    rates = _rhs(ctx, n)
+    sph.sph_sync(ctx)
+    g = sph.to_numpy(rates)
+    cur = sph.to_numpy(dev)
+    o = oracle.rhs(cur, eos, MAT, None, scales=True)
+    assert np.array_equal(g["ncount"], o["ncount"])
+    for k, v in field_errors(g, o).items():
+        assert v <= TOL_MIXED[k], (k, v)
     sph.sph_free(ctx)

@@ -6,6 +6,8 @@
   FP64 oracle on 256 random particles whose rates the oracle computes with
   brute-force neighbours over all 1e6 particles.  Their neighbour rows must
   be identical.
+* An ensemble of eight stars (about 4.8e5 particles): the same sampled check
+  of one mixed right-hand side, with and without the persistent launch.
 * The 4e6-particle crust-failure star (8 % crust, mu = 0.01 P,
   Y0 = 1e-3 mu, eps_break = 0.01, l = 2 amplitude 0.1 c_s): the same sampled
   check of one right-hand side, then a short mixed and FP64 run from one
@@ -131,3 +133,45 @@ def test_crust_4e6_flags_mixed_vs_fp64(crust4e6):
     # both runs keep all particles finite
     for k in ("x", "vx", "u", "h"):
         assert np.all(np.isfinite(out[sph.SPH_MIXED][k]))
+
+
+@pytest.fixture(scope="module")
+def ensemble8():
+    # eight stars of log-uniform size in [1e4, 2e5] (about 4.8e5 particles) in
+    # disjoint boxes of one index space
+    st, eos, met, _ = I.ensemble_state(nstars=8, seed=2107, scale_n=1.0, nr=512)
+    ids = _sample(len(st["x"]), 13)
+    o = oracle.rhs(st, eos, MAT, met, subset=ids, scales=True)
+    return st, eos, met, ids, _oracle_full(o, len(st["x"]))
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_ensemble_per_star_curves_sampled(ensemble8, persistent):
+    # Over the common box of all stars the curve leaves and re-enters each
+    # star's region, and 8-particle leaves at those jumps span much of a
+    # star: the tile walk of such a leaf then keeps several hundred 64-particle
+    # nodes, more than the tile kernel holds (SPH_ERR_CAPACITY).  Each star's
+    # key is taken over its own box, which keeps the leaves compact.
+    st, eos, met, ids, o = ensemble8
+    dev = sph.device_state(st)
+    torch.cuda.synchronize()
+    ctx = sph.sph_init(dev, eos, MAT, met, sph.SPH_MIXED, dict(OPTS, persistent=persistent),
+                       stream=stream().cuda_stream)
+    rates = sph.alloc_rates(len(st["x"]))
+    torch.cuda.synchronize()
+    sph.sph_rhs(ctx, rates)
+    sph.sph_sync(ctx)
+    g = sph.to_numpy(rates)
+    stats = sph.sph_stats(ctx)
+    assert 0 < stats[14] < 200, stats[14]
+    assert_close(g, o, TOL_MIXED, ids=ids, label="ensemble of 8")
+    offs, idx = sph.neighbors(ctx)
+    offs_o, idx_o = oracle.neighbors(st, subset=ids)
+    for k, a in enumerate(ids):
+        row = np.sort(idx[offs[a]:offs[a + 1]].astype(np.int64))
+        ref = np.asarray(idx_o[offs_o[k]:offs_o[k + 1]], dtype=np.int64)
+        assert np.array_equal(row, ref), "neighbour row of particle %d differs" % a
+    # three graph-captured steps with curve sorts and candidate reuse
+    sph.sph_step(ctx, 0.5 * I.cfl_dt(st, eos), 3)
+    sph.sph_sync(ctx)
+    sph.sph_free(ctx)

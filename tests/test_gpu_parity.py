@@ -138,11 +138,14 @@ def test_momentum_conserved_to_rounding(prec):
         assert abs(g[k].sum()) < eps * np.abs(g[k]).sum()
 
 
-@pytest.mark.parametrize("lanes", [4, 8])
-def test_lane_variants_agree(lanes):
+@pytest.mark.parametrize("prec", [sph.SPH_MIXED, sph.SPH_FP64])
+@pytest.mark.parametrize("lanes,screen", [(4, 4), (8, 4), (4, 8), (8, 8)])
+def test_lane_variants_agree(lanes, screen, prec):
+    # every launch shape the autotuner may pick, in both precisions
     st, eos = I.random_state(1500, seed=31, vel=0.2, stress=0.05)
-    opts = dict(lanes_per_particle=lanes, use_graph=1)
-    _check(st, eos, prec=sph.SPH_MIXED, tol=TOL_MIXED, options=opts, label="lanes")
+    opts = dict(lanes_per_particle=lanes, screen_lanes=screen, use_graph=1)
+    tol = TOL_MIXED if prec == sph.SPH_MIXED else TOL_FP64
+    _check(st, eos, prec=prec, tol=tol, options=opts, label="lanes")
 
 
 def test_capacity_error_is_reported():
