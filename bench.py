@@ -627,6 +627,203 @@ def mode_accuracy(dev, stream, n=20000, nsteps=1200, every=10):
                     "fitted to the central-density series of each precision's own run"}
 
 
+def _fit_omega(t, y):
+    """Angular frequency of a damped sine fitted to a sampled series (the
+    spectral peak starts the fit)."""
+    from scipy.optimize import curve_fit
+
+    y = np.asarray(y) - np.mean(y)
+    t = np.asarray(t)
+    f = np.fft.rfftfreq(len(t), t[1] - t[0])
+    amp = np.abs(np.fft.rfft(y * np.hanning(len(y))))
+    w0 = 2 * math.pi * f[1 + np.argmax(amp[1:])]
+
+    def model(x, a, w, ph, g, c0, c1):
+        return a * np.exp(-g * x) * np.sin(w * x + ph) + c0 + c1 * x
+
+    p, _ = curve_fit(model, t, y, p0=[np.abs(y).max(), w0, 0.0, 0.0, 0.0, 0.0], maxfev=20000)
+    return abs(float(p[1]))
+
+
+def _series_run(st, eos, met, prec, dt, nsteps, every, dev, stream, options):
+    """Steps one star in graph-captured steps; every `every` steps records the
+    core density (one RHS) and Q_zz = sum m (z^2 - r^2/3) about the centre of
+    mass.  Returns times, the two series, device ms per step and the state."""
+    import torch
+
+    from paper_2107_07315_gb300 import inputs as I
+    from paper_2107_07315_gb300 import sph
+
+    n = len(st["x"])
+    d = sph.device_state(st, dev)
+    torch.cuda.synchronize()
+    ctx = sph.sph_init(d, eos, I.DEFAULT_MATERIAL, met, prec, options, stream=stream.cuda_stream)
+    rates = sph.alloc_rates(n, dev)
+    r0 = np.sqrt(st["x"] ** 2 + st["y"] ** 2 + st["z"] ** 2)
+    core = torch.from_numpy(r0 < 0.2 * r0.max()).to(dev)
+    m = d["m"]
+    ms, t, rho, qzz = 0.0, [], [], []
+    for k in range(0, nsteps + 1, every):
+        if k:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                sph.sph_step(ctx, dt, every)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        with torch.cuda.stream(stream):
+            sph.sph_rhs(ctx, rates)
+        sph.sph_sync(ctx)
+        torch.cuda.synchronize()
+        t.append(k * dt)
+        rho.append(float(rates["rho"][core].mean().item()))
+        c = [float((m * d[a]).sum() / m.sum()) for a in ("x", "y", "z")]
+        x, y, z = d["x"] - c[0], d["y"] - c[1], d["z"] - c[2]
+        qzz.append(float((m * (z * z - (x * x + y * y + z * z) / 3.0)).sum()))
+    out = sph.to_numpy(d)
+    stats = sph.sph_stats(ctx)
+    sph.sph_free(ctx)
+    del d, rates
+    torch.cuda.empty_cache()
+    return np.array(t), np.array(rho), np.array(qzz), ms / nsteps, out, stats
+
+
+def campaign(args):
+    """Full-length runs of the paper-scale configurations, one JSON line each.
+
+    star1e6 : 1e6-particle star, l = 0 and l = 2 perturbations of 1e-3 c_s,
+              5000 steps in mixed precision and in FP64; radial frequency
+              from the core density, quadrupole frequency from Q_zz.
+    ensemble: the 64-star batch, 1000 mixed steps with the autotuned shape;
+              throughput and per-star conservation.
+    crust4e6: the 4e6-particle crust-failure star, 2000 steps mixed and FP64;
+              yielded and broken counts of both; and the 2e4-particle star of
+              the same configuration, FP64 GPU against the FP64 oracle over
+              `--oracle-steps` steps (flags compared exactly)."""
+    import torch
+
+    from paper_2107_07315_gb300 import inputs as I
+    from paper_2107_07315_gb300 import shard
+    from paper_2107_07315_gb300 import sph
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    opts = dict(h_nmin=55, h_nmax=65, use_graph=1, sort_every=8)
+    out = {"campaign": args.campaign}
+    if args.campaign == "star1e6":
+        steps = args.campaign_steps or 5000
+        st, eos, met, _ = I.star_state(1_000_000, seed=1, amp_l0=1e-3, amp_l2=1e-3)
+        dt = I.cfl_dt(st, eos)
+        every = max(1, steps // 250)
+        res = {}
+        for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+            t, rho, q, ms, _, stats = _series_run(st, eos, met, prec, dt, steps, every, dev, stream,
+                                                  opts)
+            res[name] = {"omega_radial": _fit_omega(t, rho), "omega_quadrupole": _fit_omega(t, q),
+                         "ms_per_step": ms, "pairs_per_step": int(stats[0])}
+        out.update({"particles": len(st["x"]), "steps": steps, "sample_every": every, "dt": dt,
+                    "mixed": res["mixed"], "fp64": res["fp64"],
+                    "radial_rel_diff": abs(res["mixed"]["omega_radial"] /
+                                           res["fp64"]["omega_radial"] - 1.0),
+                    "quadrupole_rel_diff": abs(res["mixed"]["omega_quadrupole"] /
+                                               res["fp64"]["omega_quadrupole"] - 1.0),
+                    "speedup": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]})
+    elif args.campaign == "ensemble":
+        steps = args.campaign_steps or 1000
+        full, eos_all, met_all, params = I.ensemble_state(nstars=64, seed=2107, scale_n=1.0,
+                                                          nr=1024)
+        mine = shard.assign_stars(params["N"], 1)[0]
+        st, eos, met = select_stars(full, eos_all, met_all, mine)
+        dt = 0.5 * I.cfl_dt(st, eos)
+        d = sph.device_state(st, dev)
+        torch.cuda.synchronize()
+        ctx = sph.sph_init(d, eos, I.DEFAULT_MATERIAL, met, sph.SPH_MIXED,
+                           dict(opts, lanes_per_particle=-1, persistent=-1),
+                           stream=stream.cuda_stream)
+        t0 = sph.sph_totals_per_star(ctx, len(mine))
+        p0 = sph.sph_stats(ctx)[1]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            sph.sph_step(ctx, dt, steps)
+            e1.record(stream)
+        sph.sph_sync(ctx)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = sph.sph_stats(ctx)
+        t1 = sph.sph_totals_per_star(ctx, len(mine))
+        mom0 = np.linalg.norm(t0[:, 1:4], axis=1)
+        out.update({"stars": len(mine), "particles": len(st["x"]), "steps": steps,
+                    "pairs_per_s": float(stats[1] - p0) / (ms * 1e-3), "ms_per_step": ms / steps,
+                    "launch_shape": launch_shape(stats),
+                    "max_rel_mass_change": float(np.max(np.abs(t1[:, 0] / t0[:, 0] - 1.0))),
+                    "max_rel_energy_change": float(np.max(np.abs(t1[:, 6] / t0[:, 6] - 1.0))),
+                    "max_momentum_change_over_mass": float(np.max(
+                        np.linalg.norm(t1[:, 1:4] - t0[:, 1:4], axis=1) / t0[:, 0])),
+                    "initial_momentum_over_mass_max": float(np.max(mom0 / t0[:, 0])),
+                    "yielded": int(t1[:, 10].sum()), "broken": int(t1[:, 11].sum())})
+        sph.sph_free(ctx)
+    elif args.campaign == "crust4e6":
+        import oracle
+
+        steps = args.campaign_steps or 2000
+        cfg = dict(crust_frac=0.08, mu_over_P=0.01, Y0_over_mu=1e-3, eps_break=0.01, amp_l0=0.0,
+                   amp_l2=0.1)
+        st, eos, met, _ = I.star_state(4_000_000, seed=7, **cfg)
+        dt = I.cfl_dt(st, eos)
+        crust = st["type"] == 1
+        flags = {}
+        for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+            d = sph.device_state(st, dev)
+            torch.cuda.synchronize()
+            ctx = sph.sph_init(d, eos, I.DEFAULT_MATERIAL, met, prec, opts,
+                               stream=stream.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                sph.sph_step(ctx, dt, steps)
+                e1.record(stream)
+            sph.sph_sync(ctx)
+            torch.cuda.synchronize()
+            f = d["flags"].cpu().numpy()
+            flags[name] = f
+            out[name] = {"ms_per_step": e0.elapsed_time(e1) / steps,
+                         "yielded": int(((f & 1) != 0).sum()), "broken": int(((f & 2) != 0).sum())}
+            sph.sph_free(ctx)
+            del d
+            torch.cuda.empty_cache()
+        diff = ((flags["mixed"] ^ flags["fp64"]) & 3) != 0
+        out.update({"particles": len(st["x"]), "crust_particles": int(crust.sum()), "steps": steps,
+                    "flags_differ": int(diff.sum()),
+                    "yield_flags_differ": int((((flags["mixed"] ^ flags["fp64"]) & 1) != 0).sum()),
+                    "broken_flags_differ": int((((flags["mixed"] ^ flags["fp64"]) & 2) != 0).sum())})
+        # the oracle-sized star of the same configuration: FP64 GPU vs oracle
+        k = args.oracle_steps
+        s2, e2, m2, _ = I.star_state(20000, seed=7, **cfg)
+        dt2 = I.cfl_dt(s2, e2)
+        d = sph.device_state(s2, dev)
+        torch.cuda.synchronize()
+        ctx = sph.sph_init(d, e2, I.DEFAULT_MATERIAL, m2, sph.SPH_FP64, None,
+                           stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            sph.sph_step(ctx, dt2, k)
+        sph.sph_sync(ctx)
+        g = sph.to_numpy(d)
+        sph.sph_free(ctx)
+        t0 = time.perf_counter()
+        o, _ = oracle.step(s2, e2, I.DEFAULT_MATERIAL, m2, dt2, k)
+        out["oracle_2e4"] = {"steps": k, "oracle_s": time.perf_counter() - t0,
+                             "yielded_gpu": int(((g["flags"] & 1) != 0).sum()),
+                             "yielded_oracle": int(((o["flags"] & 1) != 0).sum()),
+                             "broken_gpu": int(((g["flags"] & 2) != 0).sum()),
+                             "broken_oracle": int(((o["flags"] & 2) != 0).sum()),
+                             "flags_differ": int((g["flags"] != o["flags"]).sum()),
+                             "max_rel_pos_diff": float(np.max(np.abs(g["x"] - o["x"])) /
+                                                       np.max(np.abs(o["x"])))}
+    print(json.dumps(out), flush=True)
+
+
 def _rhs_only(tim, pairs_step):
     ms = (tim[10] / max(tim[11], 1) + tim[2] / max(tim[3], 1) + tim[0] / max(tim[1], 1))
     return {"ms": ms, "pairs_per_s": pairs_step / (ms * 1e-3) if ms > 0 else None,
@@ -833,6 +1030,12 @@ def main():
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--n", type=int, default=N_STAR)
     ap.add_argument("--workload", choices=("star", "ensemble", "relax"), default="star")
+    ap.add_argument("--campaign", choices=("star1e6", "ensemble", "crust4e6"), default=None,
+                    help="full-length paper-scale run instead of the benchmark line")
+    ap.add_argument("--campaign-steps", type=int, default=0,
+                    help="steps of the campaign (0: the configuration's own count)")
+    ap.add_argument("--oracle-steps", type=int, default=200,
+                    help="steps of the 2e4-particle oracle comparison in the crust4e6 campaign")
     ap.add_argument("--nstars", type=int, default=64)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--cpu-sample", type=int, default=0,
@@ -855,7 +1058,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.campaign:
+        campaign(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
