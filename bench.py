@@ -645,6 +645,17 @@ def _fit_omega(t, y):
     return abs(float(p[1]))
 
 
+def _cfl_dt_device(d, eos, C=0.3):
+    """dt = C min h / (c + |v|) of a device state (c from u, polytrope)."""
+    import torch
+
+    G = torch.as_tensor(np.asarray(eos["Gamma"], np.float64), device=d["u"].device)
+    g = G[d["star"].long()] if d.get("star") is not None else G[0]
+    c = torch.sqrt(torch.clamp((g - 1.0) * g * d["u"], min=0.0))
+    v = torch.sqrt(d["vx"] ** 2 + d["vy"] ** 2 + d["vz"] ** 2)
+    return float(C * torch.min(d["h"] / (c + v)).item())
+
+
 def _series_run(st, eos, met, prec, dt, nsteps, every, dev, stream, options):
     """Steps one star in graph-captured steps; every `every` steps records the
     core density (one RHS) and Q_zz = sum m (z^2 - r^2/3) about the centre of
@@ -716,12 +727,18 @@ def campaign(args):
         st, eos, met, _ = I.star_state(1_000_000, seed=1, amp_l0=1e-3, amp_l2=1e-3)
         dt = I.cfl_dt(st, eos)
         every = max(1, steps // 250)
-        res = {}
+        res, ser = {}, {}
         for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
             t, rho, q, ms, _, stats = _series_run(st, eos, met, prec, dt, steps, every, dev, stream,
                                                   opts)
+            ser[name] = (rho, q)
             res[name] = {"omega_radial": _fit_omega(t, rho), "omega_quadrupole": _fit_omega(t, q),
                          "ms_per_step": ms, "pairs_per_step": int(stats[0])}
+        # how closely the two runs' series agree, against each series' swing
+        for j, key in ((0, "core_density"), (1, "qzz")):
+            a, b = ser["mixed"][j], ser["fp64"][j]
+            out[key + "_max_diff_over_swing"] = float(np.max(np.abs(a - b)) / (np.ptp(b) or 1.0))
+        out["radial_periods_covered"] = res["fp64"]["omega_radial"] * steps * dt / (2 * math.pi)
         out.update({"particles": len(st["x"]), "steps": steps, "sample_every": every, "dt": dt,
                     "mixed": res["mixed"], "fp64": res["fp64"],
                     "radial_rel_diff": abs(res["mixed"]["omega_radial"] /
@@ -768,52 +785,75 @@ def campaign(args):
         import oracle
 
         steps = args.campaign_steps or 2000
+        chunk = 20
         cfg = dict(crust_frac=0.08, mu_over_P=0.01, Y0_over_mu=1e-3, eps_break=0.01, amp_l0=0.0,
                    amp_l2=0.1)
         st, eos, met, _ = I.star_state(4_000_000, seed=7, **cfg)
-        dt = I.cfl_dt(st, eos)
         crust = st["type"] == 1
-        flags = {}
-        for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+        flags, dts = {}, []
+        # the strong forcing compresses the crust: dt = 0.3 min h / (c + |v|)
+        # is taken again every `chunk` steps, from the FP64 run; the mixed run
+        # replays the same sequence
+        for name, prec in (("fp64", sph.SPH_FP64), ("mixed", sph.SPH_MIXED)):
             d = sph.device_state(st, dev)
             torch.cuda.synchronize()
             ctx = sph.sph_init(d, eos, I.DEFAULT_MATERIAL, met, prec, opts,
                                stream=stream.cuda_stream)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                e0.record(stream)
-                sph.sph_step(ctx, dt, steps)
-                e1.record(stream)
-            sph.sph_sync(ctx)
-            torch.cuda.synchronize()
+            ms, done, err = 0.0, 0, None
+            for k in range(0, steps, chunk):
+                if name == "fp64":
+                    dts.append(_cfl_dt_device(d, eos))
+                dt = dts[k // chunk]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    sph.sph_step(ctx, dt, min(chunk, steps - k))
+                    e1.record(stream)
+                try:
+                    sph.sph_sync(ctx)
+                except sph.SphError as e:
+                    err = str(e)
+                    break
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                done = k + min(chunk, steps - k)
             f = d["flags"].cpu().numpy()
             flags[name] = f
-            out[name] = {"ms_per_step": e0.elapsed_time(e1) / steps,
+            out[name] = {"steps_done": done, "error": err, "ms_per_step": ms / max(done, 1),
                          "yielded": int(((f & 1) != 0).sum()), "broken": int(((f & 2) != 0).sum())}
             sph.sph_free(ctx)
             del d
             torch.cuda.empty_cache()
-        diff = ((flags["mixed"] ^ flags["fp64"]) & 3) != 0
+            if name == "fp64":
+                steps = done or steps
+        diff = (flags["mixed"] ^ flags["fp64"]) & 3
         out.update({"particles": len(st["x"]), "crust_particles": int(crust.sum()), "steps": steps,
-                    "flags_differ": int(diff.sum()),
-                    "yield_flags_differ": int((((flags["mixed"] ^ flags["fp64"]) & 1) != 0).sum()),
-                    "broken_flags_differ": int((((flags["mixed"] ^ flags["fp64"]) & 2) != 0).sum())})
-        # the oracle-sized star of the same configuration: FP64 GPU vs oracle
+                    "dt_first_last_min": [dts[0], dts[-1], min(dts)],
+                    "yield_flags_differ": int(((diff & 1) != 0).sum()),
+                    "broken_flags_differ": int(((diff & 2) != 0).sum())})
+        # the oracle-sized star of the same configuration: FP64 GPU vs oracle,
+        # the same dt sequence (from the GPU state) on both
         k = args.oracle_steps
         s2, e2, m2, _ = I.star_state(20000, seed=7, **cfg)
-        dt2 = I.cfl_dt(s2, e2)
         d = sph.device_state(s2, dev)
         torch.cuda.synchronize()
         ctx = sph.sph_init(d, e2, I.DEFAULT_MATERIAL, m2, sph.SPH_FP64, None,
                            stream=stream.cuda_stream)
-        with torch.cuda.stream(stream):
-            sph.sph_step(ctx, dt2, k)
-        sph.sph_sync(ctx)
+        o = {kk: (None if v is None else np.array(v, copy=True)) for kk, v in s2.items()}
+        r_or = None  # the oracle's rates carried across chunks, as the GPU's are
+        t_or = 0.0
+        for j in range(0, k, chunk):
+            dt = _cfl_dt_device(d, e2)
+            nst = min(chunk, k - j)
+            with torch.cuda.stream(stream):
+                sph.sph_step(ctx, dt, nst)
+            sph.sph_sync(ctx)
+            t0 = time.perf_counter()
+            o, r_or = oracle.step(o, e2, I.DEFAULT_MATERIAL, m2, dt, nst, rates=r_or)
+            t_or += time.perf_counter() - t0
         g = sph.to_numpy(d)
         sph.sph_free(ctx)
-        t0 = time.perf_counter()
-        o, _ = oracle.step(s2, e2, I.DEFAULT_MATERIAL, m2, dt2, k)
-        out["oracle_2e4"] = {"steps": k, "oracle_s": time.perf_counter() - t0,
+        out["oracle_2e4"] = {"steps": k, "oracle_s": t_or,
                              "yielded_gpu": int(((g["flags"] & 1) != 0).sum()),
                              "yielded_oracle": int(((o["flags"] & 1) != 0).sum()),
                              "broken_gpu": int(((g["flags"] & 2) != 0).sum()),
@@ -1001,14 +1041,21 @@ def run_reference(args):
 
 
 def launch_shape(stats):
-    """The launch shape sph_init chose (threads per particle of the exact
-    screening and of the pair kernels, and whether screening and force run as
-    one persistent launch) and the autotuner's per-launch times; the library's
-    fixed default is 4 screening lanes, 8 pair lanes, separate launches."""
+    """The launch shape sph_init chose (the search leaf of the candidate build,
+    threads per particle of the exact screening and of the pair kernels, and
+    whether screening and force run as one persistent launch) and the
+    autotuner's per-launch times; the library's fixed default is a search
+    leaf of one tree leaf (8 particles), 4 screening lanes, 8 pair lanes,
+    separate launches."""
     src = {0: "fixed", 1: "autotuned", 2: "autotuned (process cache)"}[int(stats[20])]
-    out = {"screen_lanes": int(stats[19]), "pair_lanes": int(stats[7]),
-           "persistent_blocks": int(stats[25]), "source": src,
-           "fixed_default": {"screen_lanes": 4, "pair_lanes": 8, "persistent": False}}
+    out = {"search_leaf_particles": 8 * int(stats[31]), "screen_lanes": int(stats[19]),
+           "pair_lanes": int(stats[7]), "persistent_blocks": int(stats[25]), "source": src,
+           "fixed_default": {"search_leaf_particles": 8, "screen_lanes": 4, "pair_lanes": 8,
+                             "persistent": False}}
+    if all(v > 0 for v in stats[28:31]):
+        # one candidate-list build with search leaves of 8, 16 and 32 particles
+        out["tuner_us_build"] = {"leaf_8": int(stats[28]) / 1e3, "leaf_16": int(stats[29]) / 1e3,
+                                 "leaf_32": int(stats[30]) / 1e3}
     if stats[26] > 0 and stats[27] > 0:
         # screening + force of the chosen lanes: separate launches vs one persistent launch
         out["tuner_us_separate_vs_persistent"] = [int(stats[26]) / 1e3, int(stats[27]) / 1e3]

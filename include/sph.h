@@ -150,6 +150,12 @@ typedef struct {
  * rounding.  sph_stats reports the shape and the times.
  * screen_lanes: threads per particle of the exact screening, 4 or 8 [0: 4];
  * ignored when lanes_per_particle is -1.
+ * search_leaves: tree leaves (8 sorted particles each) that share one walk
+ * of the candidate-list search, 1, 2 or 4; the candidate lists are the same
+ * for each, only the cost of a build differs; a walk holds at most 256
+ * candidate leaves for 1 and 512 for 2 or 4 [0: 1; with lanes_per_particle
+ * -1 the autotuner times all three and takes the fastest whose walk fills at
+ * most half of its capacity on the bound state].
  * persistent: 1 runs the exact screening, density, equation of state and
  * force pass of every right-hand side as one persistent launch over a global
  * work queue of particle blocks (screening items first, then force items,
@@ -184,6 +190,7 @@ typedef struct {
     double skin;
     int32_t screen_lanes;
     int32_t persistent;
+    int32_t search_leaves;
 } sph_options;
 
 /* Create a context bound to the particle buffers.  Validates the inputs,
@@ -256,7 +263,7 @@ sph_status sph_totals_per_star(sph_ctx *ctx, double *out, int32_t nstars);
  * 7 lanes per particle, 8 1 if steps run as a CUDA graph, 9 steps taken,
  * 10 radix passes, 11 cell bits per axis of the curve key, 12 kernel
  * launches issued by sph_step (cumulative), 13 steps per curve sort,
- * 14 most candidate leaves of one leaf and 16 candidate (leaf, leaf) tiles
+ * 14 most candidate leaves of one tile-search walk and 16 candidate (leaf, leaf) tiles
  * in all (both of the last candidate-list build), 15 most neighbours of one
  * particle (last right-hand side), 17 1 for mixed precision, 18 candidate-list
  * builds so far, 19 lanes per particle of the exact screening, 20 launch
@@ -266,7 +273,9 @@ sph_status sph_totals_per_star(sph_ctx *ctx, double *out, int32_t nstars);
  * 25 blocks of the persistent right-hand-side launch (0: separate launches),
  * 26 and 27 the autotuner's times in ns of the screening and pair kernels in
  * series and of the persistent launch (zero unless persistent is -1),
- * 28-31 zero.  Synchronous. */
+ * 28-30 the autotuner's times in ns of a candidate build with search leaves
+ * of 1, 2 and 4 tree leaves (zero when not tuned), 31 tree leaves per
+ * search leaf in use.  Synchronous. */
 sph_status sph_stats(sph_ctx *ctx, int64_t out[32]);
 
 /* Device-time measurement with CUDA events on the context's stream.

@@ -83,8 +83,11 @@ struct sph_ctx {
     int tuned = 0;          // 0 fixed shape, 1 timed by sph_init, 2 from the process cache
     // autotuner times (ns per launch): screening 4 / 8 lanes, pair kernels
     // 4 / 8 lanes, screening + pair kernels in series, persistent launch
-    int64_t tune_ns[6] = {};
+    // 4 / 8 lanes, screening + pair kernels in series, persistent launch,
+    // candidate build with search leaves of 1, 2, 4 tree leaves
+    int64_t tune_ns[9] = {};
     int tune_persist = 0;   // the autotuner chose the persistent launch
+    int group = 1;          // tree leaves per tile-search walk
     PersistPlan pplan{};    // persistent right-hand side (grid 0: off)
     DevRates r{};
     double *vp = nullptr, *Sp = nullptr;
@@ -356,7 +359,7 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
     if (c->pplan.grid > 0 && !fp64) {
         // candidate lists (when stale), then screening, density, equation of
         // state and force in one persistent launch
-        launch_tiles_build(st, c->s, c->tl, c->nleaves, c->multi, c->cap, c->stream);
+        launch_tiles_build(st, c->s, c->tl, c->nleaves, c->multi, c->cap, c->stream, c->group);
         rec(c, slot_ev(c, EV_DENSITY), capturing);
         rec(c, slot_ev(c, EV_FORCE), capturing);
         launch_persistent(st, c->s, eos_of(c), c->mat, c->met, out, c->cap, c->screen_lanes,
@@ -368,7 +371,7 @@ void enqueue_rhs(sph_ctx *c, const DevState &st, const DevRates &out, bool captu
     // candidate lists (when stale) and exact lists; in mixed precision the
     // density and equation of state too
     launch_tiles(st, c->s, c->tl, c->nleaves, c->multi, c->cap, fp64 ? 0 : 1, eos_of(c), c->met,
-                 out, c->stream, nlaunch, c->screen_lanes);
+                 out, c->stream, nlaunch, c->screen_lanes, c->group);
     rec(c, slot_ev(c, EV_DENSITY), capturing);
     if (fp64) launch_density_fp64(st, c->s, eos_of(c), c->met, out, c->cap, c->lanes, c->stream);
     rec(c, slot_ev(c, EV_FORCE), capturing);
@@ -392,15 +395,18 @@ void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch, bool reso
     if (nlaunch) *nlaunch += 2;
 }
 
-// Autotuner over the launch shape: threads per particle of the exact
-// screening (4 or 8) and of the pair kernels (4 or 8), and in mixed precision
-// whether the screening and force pass run as separate launches or as one
-// persistent launch.  After one right-hand side on the bound state, sph_init
-// times each variant of each stage (three launches after a warm-up one, CUDA
-// events on the context's stream) and keeps the faster; the lane counts of
-// the two stages are chosen independently (separate kernels), then the
-// persistent launch of the chosen lanes is timed against the two stages in
-// series.  The device counters are restored afterwards, so the tuning
+// Autotuner over the launch shape: the search leaf of the candidate build
+// (1, 2 or 4 tree leaves, 8 to 32 particles, per tile-search walk), threads
+// per particle of the exact screening (4 or 8) and of the pair kernels (4 or
+// 8), and in mixed precision whether the screening and force pass run as
+// separate launches or as one persistent launch.  After one right-hand side
+// on the bound state, sph_init times each variant of each stage (three
+// launches after a warm-up one, CUDA events on the context's stream) and
+// keeps the faster; the stages are separate kernels, so they are chosen
+// independently, then the persistent launch of the chosen lanes is timed
+// against the two stages in series.  A search leaf whose walk front fills
+// more than half of its capacity on the bound state is not taken (the
+// front grows as particles move).  The device counters are restored afterwards, so the tuning
 // launches are not counted.  The choice is cached for the process under the
 // configuration (device, n, stars, precision, capacity, metric, solids, what
 // is tuned and the fixed lanes), so later contexts of the same configuration
@@ -409,8 +415,8 @@ void enqueue_step(sph_ctx *c, double dt, bool capturing, int *nlaunch, bool reso
 // rounding); the persistent launch does not change any result.
 using TuneKey = std::tuple<int, int64_t, int, int, int, int, int, int, int, int>;
 struct TuneVal {
-    int screen_lanes, lanes, persist;
-    int64_t ns[6];
+    int screen_lanes, lanes, persist, group;
+    int64_t ns[9];
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -444,7 +450,8 @@ sph_status autotune_shape(sph_ctx *c, bool lanes, bool persist)
             c->screen_lanes = it->second.screen_lanes;
             c->lanes = it->second.lanes;
             c->tune_persist = it->second.persist;
-            for (int k = 0; k < 6; ++k) c->tune_ns[k] = it->second.ns[k];
+            if (lanes) c->group = it->second.group;
+            for (int k = 0; k < 9; ++k) c->tune_ns[k] = it->second.ns[k];
             c->tuned = 2;
             return SPH_OK;
         }
@@ -477,6 +484,39 @@ sph_status autotune_shape(sph_ctx *c, bool lanes, bool persist)
             c->screen_lanes = c->tune_ns[1] < c->tune_ns[0] ? 8 : 4;
             c->lanes = c->tune_ns[3] < c->tune_ns[2] ? 8 : 4;
         }
+        // candidate builds (the rebuild flag set before each launch)
+        const int groups[3] = {1, 2, 4};
+        const int caps[3] = {kCandCap, 2 * kCandCap, 2 * kCandCap};
+        static const int one = 1;
+        int best = 1;
+        int64_t best_ns = 0;
+        for (int k = 0; k < 3 && rc == SPH_OK; ++k) {
+            const int gk = groups[k];
+            rc = time_stage(c, e0, e1, &c->tune_ns[6 + k], [&] {
+                cudaMemcpyAsync(&c->s.sc->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice,
+                                c->stream);
+                launch_tiles_build(st, c->s, c->tl, c->nleaves, c->multi, c->cap, c->stream, gk);
+            });
+            if (rc != SPH_OK) break;
+            DevScalars now{};
+            if (cudaMemcpy(&now, c->s.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = fail(SPH_ERR_CUDA, "autotune: reading the counters failed");
+                break;
+            }
+            const bool fits = !(now.err & ERR_CAPACITY) && 2 * now.max_cand <= caps[k];
+            if (fits && (k == 0 || c->tune_ns[6 + k] < best_ns)) {
+                best = gk;
+                best_ns = c->tune_ns[6 + k];
+            }
+            // the next variant starts from clean counters
+            now.err &= ~ERR_CAPACITY;
+            now.max_cand = 0;
+            if (cudaMemcpy(c->s.sc, &now, sizeof(DevScalars), cudaMemcpyHostToDevice) != cudaSuccess) {
+                rc = fail(SPH_ERR_CUDA, "autotune: resetting the counters failed");
+                break;
+            }
+        }
+        if (rc == SPH_OK) c->group = best;
     }
     if (persist && rc == SPH_OK) {
         const PersistPlan pp = plan_persistent(c->n, c->screen_lanes, c->lanes);
@@ -502,8 +542,8 @@ sph_status autotune_shape(sph_ctx *c, bool lanes, bool persist)
     CUDA_TRY(cudaMemcpy(c->s.sc, &saved, sizeof(DevScalars), cudaMemcpyHostToDevice));
     c->tuned = 1;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    TuneVal v{c->screen_lanes, c->lanes, c->tune_persist, {}};
-    for (int k = 0; k < 6; ++k) v.ns[k] = c->tune_ns[k];
+    TuneVal v{c->screen_lanes, c->lanes, c->tune_persist, c->group, {}};
+    for (int k = 0; k < 9; ++k) v.ns[k] = c->tune_ns[k];
     g_tune_cache.emplace(key, v);
     return SPH_OK;
 }
@@ -627,6 +667,9 @@ sph_status validate(const sph_particles *p, const sph_eos *eos, const sph_materi
             return fail(SPH_ERR_ARG, "screen_lanes must be 0, 4 or 8");
         if (opt->persistent < -1 || opt->persistent > 1)
             return fail(SPH_ERR_ARG, "persistent must be -1, 0 or 1");
+        if (opt->search_leaves != 0 && opt->search_leaves != 1 && opt->search_leaves != 2 &&
+            opt->search_leaves != 4)
+            return fail(SPH_ERR_ARG, "search_leaves must be 0, 1, 2 or 4");
         if (opt->h_nmax < 0 || opt->h_nmin < 0 || (opt->h_nmax > 0 && opt->h_nmin > opt->h_nmax))
             return fail(SPH_ERR_ARG, "h_nmin/h_nmax band invalid");
         if (opt->sort_every < 0) return fail(SPH_ERR_ARG, "sort_every must be >= 0");
@@ -652,6 +695,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : kRowCap;
     c->lanes = c->opt.lanes_per_particle > 0 ? c->opt.lanes_per_particle : 8;
     c->screen_lanes = c->opt.screen_lanes > 0 ? c->opt.screen_lanes : 4;
+    c->group = c->opt.search_leaves > 0 ? c->opt.search_leaves : 1;
     c->stream = (cudaStream_t)stream;
     if (prec == SPH_MIXED) {
         CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
@@ -993,12 +1037,14 @@ sph_status sph_sync(sph_ctx *c)
         if (err & ERR_NONFINITE) return fail(SPH_ERR_NONFINITE, "non-finite position, velocity or h");
         // a timed-out sort is the cause of any bounds flag raised with it
         if (err & ERR_TIMEOUT)
-            return fail(SPH_ERR_TIMEOUT, "a sort pass gave up waiting for a predecessor tile");
+            return fail(SPH_ERR_TIMEOUT,
+                        "a device-side wait gave up (a sort pass waiting for a predecessor "
+                        "tile, or a force item of the persistent launch)");
         if (err & ERR_CAPACITY)
             return fail(SPH_ERR_CAPACITY,
-                        "a particle has more than max_neighbors = %d neighbours, or a leaf more "
-                        "than %d candidate leaves",
-                        c->cap, kCandCap);
+                        "a particle has more than max_neighbors = %d neighbours, or a "
+                        "tile-search walk more than %d candidate leaves",
+                        c->cap, c->group > 1 ? 2 * kCandCap : kCandCap);
         if (err & ERR_BOUNDS) return fail(SPH_ERR_BOUNDS, "index out of bounds");
     }
     return SPH_OK;
@@ -1177,6 +1223,8 @@ sph_status sph_stats(sph_ctx *c, int64_t out[32])
     out[25] = c->pplan.grid;
     out[26] = c->tune_ns[4];
     out[27] = c->tune_ns[5];
+    for (int k = 0; k < 3; ++k) out[28 + k] = c->tune_ns[6 + k];
+    out[31] = c->group;
     return SPH_OK;
 }
 

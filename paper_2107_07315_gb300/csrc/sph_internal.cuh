@@ -264,7 +264,7 @@ void launch_build(const DevState &st, const Scratch &s, const SortPlan &plan,
 void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
                   int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
                   const DevRates &out, cudaStream_t stream, int *nlaunch = nullptr,
-                  int screen_lanes = 4);
+                  int screen_lanes = 4, int group = 1);
 
 // Exact screening (with the density and equation of state when density is
 // true) alone, from the candidate lists of the last build; the autotuner
@@ -275,8 +275,10 @@ void launch_screen(const DevState &st, const Scratch &s, int cap, int density,
 
 // Candidate-list build alone (the kernel returns at once unless the tree
 // kernel asked for a rebuild).
+// group: tree leaves per tile-search walk (1, 2 or 4: a search leaf of 8, 16
+// or 32 particles; the candidate lists are the same for each).
 void launch_tiles_build(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
-                        int multi_star, int cap, cudaStream_t stream);
+                        int multi_star, int cap, cudaStream_t stream, int group = 1);
 
 // Persistent right-hand side, mixed precision (one launch): grid blocks
 // dequeue items from a global counter; items 0 .. nA-1 screen a block of

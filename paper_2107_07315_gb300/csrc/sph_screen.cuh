@@ -104,12 +104,23 @@ __device__ __forceinline__ void screen_block(const DevState &st, const Scratch &
             // them.  This round's hits hold ranks pos .. pos + nh - 1; the one
             // of rank = sub (mod LPI) is hit number idx, on lane src of the group.
             const int idx = (sub - pos) & (LPI - 1);
-            int src = sub, c = 0;
+            int src = sub;
+            if (LPI == 4) {
+                // position of the (idx+1)-th set bit of the 4-bit mask: a
+                // table of 2-bit entries indexed by (bits, idx), 0 where the
+                // mask has fewer set bits (any lane serves then)
+                const unsigned key = (bits << 2) | (unsigned)idx;
+                const unsigned long long lut =
+                    key < 32u ? 0x2409080204010000ull : 0xe439380e340d0c03ull;
+                src = (int)((lut >> (2u * (key & 31u))) & 3ull);
+            } else {
+                int c = 0;
 #pragma unroll
-            for (int bq = 0; bq < LPI; ++bq) {
-                if ((bits >> bq) & 1u) {
-                    if (c == idx) src = bq;
-                    ++c;
+                for (int bq = 0; bq < LPI; ++bq) {
+                    if ((bits >> bq) & 1u) {
+                        if (c == idx) src = bq;
+                        ++c;
+                    }
                 }
             }
             const float tv = __shfl_sync(0xffffffffu, term, (int)gshift + src);

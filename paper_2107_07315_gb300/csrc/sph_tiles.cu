@@ -68,25 +68,59 @@ namespace sph {
 
 namespace {
 
-constexpr int kTileWarps = 4;
-constexpr int kTileThreads = 32 * kTileWarps;
 constexpr int kChunk = 4;  // candidate leaves staged per chunk (32 particles)
-template <bool MULTI_STAR>
-__global__ void __launch_bounds__(kTileThreads, 8)
+
+// Shape of the tile search: G consecutive tree leaves (a search leaf of 8 G
+// particles) share one walk, whose front holds at most kCap candidate
+// leaves; kWarps warps per block (one walk per warp).  The candidate lists
+// are the same for every G (see k_tiles); G sets only the cost of a build.
+template <int G>
+struct TileShape;
+template <>
+struct TileShape<1> {
+    static constexpr int kWarps = 4, kCap = kCandCap, kMinBlocks = 8;
+    using Reach = unsigned char;
+};
+template <>
+struct TileShape<2> {
+    static constexpr int kWarps = 2, kCap = 2 * kCandCap, kMinBlocks = 12;
+    using Reach = unsigned short;
+};
+template <>
+struct TileShape<4> {
+    static constexpr int kWarps = 2, kCap = 2 * kCandCap, kMinBlocks = 12;
+    using Reach = unsigned int;
+};
+
+// One warp per search leaf of G tree leaves.  The walk uses the union of the
+// G leaf boxes and their star range at inner levels and the reach mask of
+// all 8 G particles at the leaf level.  Then, leaf by leaf, the candidate
+// leaves that one of its own particles reaches (and, several stars, that
+// belong to its star) are screened in tiles and decoded as for one leaf.  A
+// leaf B reached by a particle q of leaf A is also kept by a walk of A alone
+// (q lies in A's box, and every ancestor of B has a larger box and h_max),
+// and both tests pass exactly the same pairs, so the candidate lists do not
+// depend on G.
+template <bool MULTI_STAR, int G>
+__global__ void __launch_bounds__(32 * TileShape<G>::kWarps, TileShape<G>::kMinBlocks)
 k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
 {
-    __shared__ int s_front[kTileWarps][2][kCandCap];
-    __shared__ unsigned char s_reach[kTileWarps][2][kCandCap];
-    __shared__ float4 s_p[kTileWarps][kLeaf];        // A's fl32 positions and h (walk)
-    __shared__ float4 s_A[kTileWarps][kLeaf][2];     // A's records (Xhi, h), (Xlo, m)
-    __shared__ float4 s_stage[kTileWarps][2][kChunk * kLeaf];  // (X, h) relative to A's first particle
-    __shared__ int2 s_lr[kTileWarps][2][kChunk];
-    __shared__ uint2 s_mask[kTileWarps][kCandCap];   // tile masks: rows 0-3, rows 4-7
+    constexpr int W = TileShape<G>::kWarps, CAP = TileShape<G>::kCap, NP = kLeaf * G;
+    using Reach = typename TileShape<G>::Reach;
+    __shared__ int s_front[W][2][CAP];
+    __shared__ Reach s_reach[W][2][CAP];
+    __shared__ float4 s_p[W][NP];        // the group's fl32 positions and h (walk)
+    __shared__ float4 s_A[W][NP][2];     // the group's records (Xhi, h), (Xlo, m)
+    __shared__ float4 s_stage[W][2][kChunk * kLeaf];  // (X, h) relative to A's first particle
+    __shared__ int2 s_lr[W][2][kChunk];
+    __shared__ uint2 s_mask[W][CAP];     // tile masks of one leaf: rows 0-3, rows 4-7
+    __shared__ short s_sel[W][G > 1 ? CAP : 1];  // front slots of one leaf (G > 1)
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int A = blockIdx.x * kTileWarps + w;
+    const int A0 = (blockIdx.x * W + w) * G;
     // whole warps only (no block-wide barrier below); nothing consumes an
     // order whose sort timed out; nothing to do while the lists are valid
-    if (A >= nleaves || order_invalid(s.sc) || !s.sc->rebuild) return;
+    if (A0 >= nleaves || order_invalid(s.sc) || !s.sc->rebuild) return;
+    const int ng = min(G, nleaves - A0);
     const int64_t n = st.n;
     const unsigned lt = (1u << lane) - 1u;
     DevScalars *sc = s.sc;
@@ -94,37 +128,72 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
     const float band_abs = sc->band_abs;
     const float scale = 1.f + fmaxf(sc->skin, 0.f);  // s = 1 + eps of the candidate lists
 
-    const int2 ar = leaf_range<MULTI_STAR>(s.leaf_start, A, n);
-    const int na = ar.y - ar.x;
-    if (lane < kLeaf) {
-        const bool v = lane < na;
-        s_p[w][lane] = v ? s.pos4[ar.x + lane] : make_float4(3e38f, 3e38f, 3e38f, 0.f);
-        s_A[w][lane][0] = v ? s.rec[ar.x + lane] : make_float4(3e38f, 3e38f, 3e38f, 0.f);
-        s_A[w][lane][1] = v ? s.rec[n + ar.x + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the group's particles: lane 8 g + k holds particle k of leaf A0 + g
+    bool pv = false;
+    if (lane < NP) {
+        const int g = lane / kLeaf, k = lane % kLeaf;
+        int64_t ip = 0;
+        if (g < ng) {
+            const int2 r = leaf_range<MULTI_STAR>(s.leaf_start, A0 + g, n);
+            pv = k < r.y - r.x;
+            ip = r.x + k;
+        }
+        s_p[w][lane] = pv ? s.pos4[ip] : make_float4(3e38f, 3e38f, 3e38f, 0.f);
+        s_A[w][lane][0] = pv ? s.rec[ip] : make_float4(3e38f, 3e38f, 3e38f, 0.f);
+        s_A[w][lane][1] = pv ? s.rec[n + ip] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const int64_t a_node = 2 * (int64_t)tl.offset[0] + 2 * (int64_t)A;
-    const float4 Alo = s.nodes[a_node], Ahi = s.nodes[a_node + 1];
-    const int astar = MULTI_STAR ? s.leaf_star[A] : 0;
+    const unsigned pmask = __ballot_sync(0xffffffffu, pv);
+    // the group's box (union of its leaf boxes, h_max in lo.w) and star range
+    float4 Glo = make_float4(3e38f, 3e38f, 3e38f, 0.f), Ghi = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+    int slo = 0x7fffffff, shi = -1;
+    if (lane < ng) {
+        const int64_t a_node = 2 * (int64_t)tl.offset[0] + 2 * (int64_t)(A0 + lane);
+        Glo = s.nodes[a_node];
+        Ghi = s.nodes[a_node + 1];
+        slo = shi = MULTI_STAR ? s.leaf_star[A0 + lane] : 0;
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        Glo.x = fminf(Glo.x, __shfl_xor_sync(0xffffffffu, Glo.x, o));
+        Glo.y = fminf(Glo.y, __shfl_xor_sync(0xffffffffu, Glo.y, o));
+        Glo.z = fminf(Glo.z, __shfl_xor_sync(0xffffffffu, Glo.z, o));
+        Glo.w = fmaxf(Glo.w, __shfl_xor_sync(0xffffffffu, Glo.w, o));
+        Ghi.x = fmaxf(Ghi.x, __shfl_xor_sync(0xffffffffu, Ghi.x, o));
+        Ghi.y = fmaxf(Ghi.y, __shfl_xor_sync(0xffffffffu, Ghi.y, o));
+        Ghi.z = fmaxf(Ghi.z, __shfl_xor_sync(0xffffffffu, Ghi.z, o));
+        slo = min(slo, __shfl_xor_sync(0xffffffffu, slo, o));
+        shi = max(shi, __shfl_xor_sync(0xffffffffu, shi, o));
+    }
+    Glo.x = __shfl_sync(0xffffffffu, Glo.x, 0);
+    Glo.y = __shfl_sync(0xffffffffu, Glo.y, 0);
+    Glo.z = __shfl_sync(0xffffffffu, Glo.z, 0);
+    Glo.w = __shfl_sync(0xffffffffu, Glo.w, 0);
+    Ghi.x = __shfl_sync(0xffffffffu, Ghi.x, 0);
+    Ghi.y = __shfl_sync(0xffffffffu, Ghi.y, 0);
+    Ghi.z = __shfl_sync(0xffffffffu, Ghi.z, 0);
+    slo = __shfl_sync(0xffffffffu, slo, 0);
+    shi = __shfl_sync(0xffffffffu, shi, 0);
     __syncwarp();
 
     // ---------------------------------------------------------------- walk
     auto box_box = [&](const float4 &lo, const float4 &hi) -> bool {
         if (MULTI_STAR) {
             const int sr = __float_as_int(hi.w);
-            if (astar < (sr & 0xffff) || astar > (int)((unsigned)sr >> 16)) return false;
+            if (shi < (sr & 0xffff) || slo > (int)((unsigned)sr >> 16)) return false;
         }
-        const float gx = fmaxf(fmaxf(lo.x - Ahi.x, Alo.x - hi.x), 0.f);
-        const float gy = fmaxf(fmaxf(lo.y - Ahi.y, Alo.y - hi.y), 0.f);
-        const float gz = fmaxf(fmaxf(lo.z - Ahi.z, Alo.z - hi.z), 0.f);
-        const float R = fmaf((Alo.w + lo.w) * scale, 1.0001f, eps);
+        const float gx = fmaxf(fmaxf(lo.x - Ghi.x, Glo.x - hi.x), 0.f);
+        const float gy = fmaxf(fmaxf(lo.y - Ghi.y, Glo.y - hi.y), 0.f);
+        const float gz = fmaxf(fmaxf(lo.z - Ghi.z, Glo.z - hi.z), 0.f);
+        const float R = fmaf((Glo.w + lo.w) * scale, 1.0001f, eps);
         return fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
     };
-    // particles of A within h_q + h_max of a leaf box (fl32 positions; leaf
-    // boxes hold every FP64 position and h; the slack covers FP32 rounding)
-    auto reach8 = [&](const float4 &lo, const float4 &hi) -> unsigned {
+    // particles of the group within h_q + h_max of a leaf box (fl32
+    // positions; leaf boxes hold every FP64 position and h; the slack
+    // covers FP32 rounding)
+    auto reach_mask = [&](const float4 &lo, const float4 &hi) -> unsigned {
         unsigned r = 0u;
 #pragma unroll
-        for (int k = 0; k < kLeaf; ++k) {
+        for (int k = 0; k < NP; ++k) {
             const float4 pk = s_p[w][k];
             const float gx = fmaxf(fmaxf(lo.x - pk.x, pk.x - hi.x), 0.f);
             const float gy = fmaxf(fmaxf(lo.y - pk.y, pk.y - hi.y), 0.f);
@@ -135,10 +204,10 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
         return r;
     };
     int *front = s_front[w][0], *next = s_front[w][1];
-    unsigned char *rfront = s_reach[w][0], *rnext = s_reach[w][1];
+    Reach *rfront = s_reach[w][0], *rnext = s_reach[w][1];
     if (lane == 0) {
         front[0] = 0;  // the root (at level 0 when the tree is one leaf)
-        rfront[0] = (unsigned char)((1u << na) - 1u);
+        rfront[0] = (Reach)pmask;
     }
     int F = 1;
     bool over = false;
@@ -170,59 +239,37 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
             const float4 lo = lon, hi = hin;
             if (t0 + 32 < total) fetch(t0 + 32 + lane);
             unsigned r = 0u;
-            if (v && box_box(lo, hi)) r = leaves ? reach8(lo, hi) : 1u;
+            if (v && box_box(lo, hi)) r = leaves ? reach_mask(lo, hi) : 1u;
             const bool hit = r != 0u;
             const unsigned bal = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 const int pos = nf + __popc(bal & lt);
-                if (pos < kCandCap) {
+                if (pos < CAP) {
                     next[pos] = c;
-                    rnext[pos] = (unsigned char)r;
+                    rnext[pos] = (Reach)r;
                 }
             }
             nf += __popc(bal);
         }
-        if (nf > kCandCap) {
+        if (nf > CAP) {
             over = true;
-            nf = kCandCap;
+            nf = CAP;
         }
         __syncwarp();
         int *tmp = front;
         front = next;
         next = tmp;
-        unsigned char *rt = rfront;
+        Reach *rt = rfront;
         rfront = rnext;
         rnext = rt;
         F = nf;
     }
     const int nc = F;
-    if (lane == 0) {
-        atomicMax(&sc->max_cand, nc);
-        atomicAdd(&sc->tiles_last, (unsigned long long)nc);
-    }
+    if (lane == 0) atomicMax(&sc->max_cand, nc);
 
-    // --------------------------------------------------------------- tiles
-    // FP32 coordinates relative to A's first particle O, and the band of this
-    // leaf (48 u (g + e), e the largest extent of A's box)
-    const float4 O0 = s_A[w][0][0], O1 = s_A[w][0][1];
-    auto rel = [&](const float4 &r0, const float4 &r1) -> float4 {
-        return make_float4((r0.x - O0.x) + (r1.x - O1.x), (r0.y - O0.y) + (r1.y - O1.y),
-                           (r0.z - O0.z) + (r1.z - O1.z), r0.w);
-    };
-    const float ext = fmaxf(fmaxf(Ahi.x - Alo.x, Ahi.y - Alo.y), Ahi.z - Alo.z);
-    const float band = fmaf(48.f * 5.9604645e-8f, ext, band_abs);
-    // screening lanes: lane 8 hr + jj takes particle jj of B against rows hr
-    // and hr + 4 of A
-    const int hr = lane >> 3, jj = lane & 7;
-    const bool v0 = hr < na, v1 = hr + 4 < na;
-    // missing rows and missing staged particles sit far apart on opposite
-    // sides: such a pair is never a hit and never inside the band
-    const float4 x0 = v0 ? rel(s_A[w][hr][0], s_A[w][hr][1]) : make_float4(3e18f, 3e18f, 3e18f, 0.f);
-    const float4 x1 = v1 ? rel(s_A[w][hr + 4][0], s_A[w][hr + 4][1])
-                         : make_float4(3e18f, 3e18f, 3e18f, 0.f);
     // candidate test of row x with staged particle b: FP32 distance below
     // s (h_a + h_b), or within the FP32 error band of it
-    auto pair = [&](const float4 &x, const float4 &bq) -> bool {
+    auto pair = [&](const float4 &x, const float4 &bq, float band) -> bool {
         const float dx = x.x - bq.x, dy = x.y - bq.y, dz = x.z - bq.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float hs = (x.w + bq.w) * scale;
@@ -230,87 +277,139 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
         const float M = fmaf(kBandRel, r2 + hs2, band * hs);
         return r2 - hs2 < M;
     };
-
-    float4 nb4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    int2 nlr = make_int2(0, 0);
-    auto load_chunk = [&](int c0) {
-        const int slot = c0 + (lane >> 3), b = lane & 7;
-        nb4 = make_float4(-3e18f, -3e18f, -3e18f, 0.f);
-        if (slot < nc) {
-            const int2 lr = leaf_range<MULTI_STAR>(s.leaf_start, front[slot], n);
-            if (b < lr.y - lr.x) nb4 = rel(s.rec[lr.x + b], s.rec[n + lr.x + b]);
-        }
-        nlr = make_int2(0, 0);
-        if (lane < kChunk && c0 + lane < nc) nlr = leaf_range<MULTI_STAR>(s.leaf_start, front[c0 + lane], n);
-    };
-    load_chunk(0);
-    for (int c0 = 0; c0 < nc; c0 += kChunk) {
-        const int buf = (c0 / kChunk) & 1;
-        s_stage[w][buf][lane] = nb4;
-        if (lane < kChunk) s_lr[w][buf][lane] = nlr;
-        __syncwarp();
-        if (c0 + kChunk < nc) load_chunk(c0 + kChunk);
-        const int kend = min(kChunk, nc - c0);
-        uint2 mk = make_uint2(0u, 0u);  // lane k < kChunk: mask of slot c0 + k
-#pragma unroll
-        for (int k = 0; k < kChunk; ++k) {
-            if (k >= kend) break;  // warp-uniform
-            const int2 lr = s_lr[w][buf][k];
-            const unsigned reach = rfront[c0 + k];
-            const float4 bq = s_stage[w][buf][k * kLeaf + jj];
-            unsigned b0 = 0u, b1 = 0u;
-            if (reach & 0x0fu) b0 = __ballot_sync(0xffffffffu, pair(x0, bq));
-            if (reach & 0xf0u) b1 = __ballot_sync(0xffffffffu, pair(x1, bq));
-            if (lr.x == ar.x) {  // the self tile: particle q is not its own neighbour
-                b0 &= ~0x08040201u;
-                b1 &= ~0x80402010u;
-            }
-            if (lane == k) mk = make_uint2(b0, b1);
-        }
-        if (lane < kend) s_mask[w][c0 + lane] = mk;
-    }
-    __syncwarp();
-
-    // decode: lane 4q + s4 takes tiles s4, s4 + 4, ... of row q; a 4-lane
-    // prefix of the hit counts places each tile's entries, so the list of
-    // row q is ascending
+    const int hr = lane >> 3, jj = lane & 7;
     const int q = lane >> 2, s4 = lane & 3;
-    const bool vq = q < na;
-    const int64_t i = ar.x + (vq ? q : 0);
-    int32_t *lq = s.vlist + i * cap;
-    int cnt = 0;
-    for (int k0 = 0; k0 < nc; k0 += 4) {
-        const int k = k0 + s4;
-        unsigned byte = 0u;
-        int start = 0;
-        if (k < nc) {
-            const uint2 m = s_mask[w][k];
-            byte = ((q < 4 ? m.x : m.y) >> (8 * (q & 3))) & 0xffu;
-            start = leaf_range<MULTI_STAR>(s.leaf_start, front[k], n).x;
-        }
-        const int c = __popc(byte);
-        int pre = c;
-        for (int o = 1; o < 4; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, pre, o, 4);
-            if (s4 >= o) pre += y;
-        }
-        int p = cnt + pre - c;
-        cnt += __shfl_sync(0xffffffffu, pre, 3, 4);
-        while (byte) {
-            const int b = __ffs(byte) - 1;
-            byte &= byte - 1u;
-            if (p < cap) lq[p] = start + b;
-            ++p;
-        }
-    }
 
-    // ------------------------------------------------- per-particle results
-    if (vq && cnt > cap) over = true;
-    if (vq && s4 == 0) {
-        s.vcnt[i] = min(cnt, cap);
-        const float4 p = s_p[w][q];
-        s.pos_build[i] = p;  // the positions and h these lists hold for
-        atomicMin((unsigned *)&sc->hmin_build, __float_as_uint(p.w));
+    for (int g = 0; g < ng; ++g) {
+        const int A = A0 + g;
+        const int2 ar = leaf_range<MULTI_STAR>(s.leaf_start, A, n);
+        const int na = ar.y - ar.x;
+        // the front slots whose leaf one of A's particles reaches (and, several
+        // stars, of A's star); every slot for a search leaf of one tree leaf
+        int ncg = nc;
+        if (G > 1) {
+            const int astar = MULTI_STAR ? s.leaf_star[A] : 0;
+            ncg = 0;
+            for (int t0 = 0; t0 < nc; t0 += 32) {
+                const int t = t0 + lane;
+                bool keep = false;
+                if (t < nc) {
+                    keep = (((unsigned)rfront[t] >> (kLeaf * g)) & 0xffu) != 0u;
+                    if (MULTI_STAR && keep) keep = s.leaf_star[front[t]] == astar;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) s_sel[w][ncg + __popc(bal & lt)] = (short)t;
+                ncg += __popc(bal);
+            }
+            __syncwarp();
+        }
+        auto slot_of = [&](int c) -> int { return G > 1 ? (int)s_sel[w][c] : c; };
+        if (lane == 0) atomicAdd(&sc->tiles_last, (unsigned long long)ncg);
+
+        // ----------------------------------------------------------- tiles
+        // FP32 coordinates relative to A's first particle O, and the band of
+        // this leaf (48 u (g + e), e the largest extent of A's box)
+        const int64_t a_node = 2 * (int64_t)tl.offset[0] + 2 * (int64_t)A;
+        const float4 Alo = s.nodes[a_node], Ahi = s.nodes[a_node + 1];
+        const float4 O0 = s_A[w][kLeaf * g][0], O1 = s_A[w][kLeaf * g][1];
+        auto rel = [&](const float4 &r0, const float4 &r1) -> float4 {
+            return make_float4((r0.x - O0.x) + (r1.x - O1.x), (r0.y - O0.y) + (r1.y - O1.y),
+                               (r0.z - O0.z) + (r1.z - O1.z), r0.w);
+        };
+        const float ext = fmaxf(fmaxf(Ahi.x - Alo.x, Ahi.y - Alo.y), Ahi.z - Alo.z);
+        const float band = fmaf(48.f * 5.9604645e-8f, ext, band_abs);
+        // screening lanes: lane 8 hr + jj takes particle jj of B against rows
+        // hr and hr + 4 of A; missing rows and missing staged particles sit
+        // far apart on opposite sides: such a pair is never a hit and never
+        // inside the band
+        const bool v0 = hr < na, v1 = hr + 4 < na;
+        const float4 x0 = v0 ? rel(s_A[w][kLeaf * g + hr][0], s_A[w][kLeaf * g + hr][1])
+                             : make_float4(3e18f, 3e18f, 3e18f, 0.f);
+        const float4 x1 = v1 ? rel(s_A[w][kLeaf * g + hr + 4][0], s_A[w][kLeaf * g + hr + 4][1])
+                             : make_float4(3e18f, 3e18f, 3e18f, 0.f);
+
+        float4 nb4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int2 nlr = make_int2(0, 0);
+        auto load_chunk = [&](int c0) {
+            const int slot = c0 + (lane >> 3), b = lane & 7;
+            nb4 = make_float4(-3e18f, -3e18f, -3e18f, 0.f);
+            if (slot < ncg) {
+                const int2 lr = leaf_range<MULTI_STAR>(s.leaf_start, front[slot_of(slot)], n);
+                if (b < lr.y - lr.x) nb4 = rel(s.rec[lr.x + b], s.rec[n + lr.x + b]);
+            }
+            nlr = make_int2(0, 0);
+            if (lane < kChunk && c0 + lane < ncg)
+                nlr = leaf_range<MULTI_STAR>(s.leaf_start, front[slot_of(c0 + lane)], n);
+        };
+        load_chunk(0);
+        for (int c0 = 0; c0 < ncg; c0 += kChunk) {
+            const int buf = (c0 / kChunk) & 1;
+            s_stage[w][buf][lane] = nb4;
+            if (lane < kChunk) s_lr[w][buf][lane] = nlr;
+            __syncwarp();
+            if (c0 + kChunk < ncg) load_chunk(c0 + kChunk);
+            const int kend = min(kChunk, ncg - c0);
+            uint2 mk = make_uint2(0u, 0u);  // lane k < kChunk: mask of slot c0 + k
+#pragma unroll
+            for (int k = 0; k < kChunk; ++k) {
+                if (k >= kend) break;  // warp-uniform
+                const int2 lr = s_lr[w][buf][k];
+                const unsigned reach = ((unsigned)rfront[slot_of(c0 + k)] >> (kLeaf * g)) & 0xffu;
+                const float4 bq = s_stage[w][buf][k * kLeaf + jj];
+                unsigned b0 = 0u, b1 = 0u;
+                if (reach & 0x0fu) b0 = __ballot_sync(0xffffffffu, pair(x0, bq, band));
+                if (reach & 0xf0u) b1 = __ballot_sync(0xffffffffu, pair(x1, bq, band));
+                if (lr.x == ar.x) {  // the self tile: particle q is not its own neighbour
+                    b0 &= ~0x08040201u;
+                    b1 &= ~0x80402010u;
+                }
+                if (lane == k) mk = make_uint2(b0, b1);
+            }
+            if (lane < kend) s_mask[w][c0 + lane] = mk;
+        }
+        __syncwarp();
+
+        // decode: lane 4q + s4 takes tiles s4, s4 + 4, ... of row q; a 4-lane
+        // prefix of the hit counts places each tile's entries, so the list of
+        // row q is ascending
+        const bool vq = q < na;
+        const int64_t i = ar.x + (vq ? q : 0);
+        int32_t *lq = s.vlist + i * cap;
+        int cnt = 0;
+        for (int k0 = 0; k0 < ncg; k0 += 4) {
+            const int k = k0 + s4;
+            unsigned byte = 0u;
+            int start = 0;
+            if (k < ncg) {
+                const uint2 m = s_mask[w][k];
+                byte = ((q < 4 ? m.x : m.y) >> (8 * (q & 3))) & 0xffu;
+                start = leaf_range<MULTI_STAR>(s.leaf_start, front[slot_of(k)], n).x;
+            }
+            const int c = __popc(byte);
+            int pre = c;
+            for (int o = 1; o < 4; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, pre, o, 4);
+                if (s4 >= o) pre += y;
+            }
+            int p = cnt + pre - c;
+            cnt += __shfl_sync(0xffffffffu, pre, 3, 4);
+            while (byte) {
+                const int b = __ffs(byte) - 1;
+                byte &= byte - 1u;
+                if (p < cap) lq[p] = start + b;
+                ++p;
+            }
+        }
+
+        // --------------------------------------------- per-particle results
+        if (vq && cnt > cap) over = true;
+        if (vq && s4 == 0) {
+            s.vcnt[i] = min(cnt, cap);
+            const float4 p = s_p[w][kLeaf * g + q];
+            s.pos_build[i] = p;  // the positions and h these lists hold for
+            atomicMin((unsigned *)&sc->hmin_build, __float_as_uint(p.w));
+        }
+        __syncwarp();  // s_stage, s_lr, s_mask and s_sel are reused by the next leaf
     }
     if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&sc->err, ERR_CAPACITY);
 }
@@ -344,21 +443,32 @@ void launch_screen(const DevState &st, const Scratch &s, int cap, int density,
     }
 }
 
+template <int G>
+static void launch_tiles_g(const DevState &st, const Scratch &s, const TreeLevels &tl,
+                           int nleaves, int multi_star, int cap, cudaStream_t stream)
+{
+    constexpr int W = TileShape<G>::kWarps;
+    const int nb = (nleaves + W * G - 1) / (W * G);
+    if (multi_star) k_tiles<true, G><<<nb, 32 * W, 0, stream>>>(st, s, tl, nleaves, cap);
+    else k_tiles<false, G><<<nb, 32 * W, 0, stream>>>(st, s, tl, nleaves, cap);
+}
+
 void launch_tiles_build(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
-                        int multi_star, int cap, cudaStream_t stream)
+                        int multi_star, int cap, cudaStream_t stream, int group)
 {
     if (nleaves <= 0) return;
-    const int nb = (nleaves + kTileWarps - 1) / kTileWarps;
-    if (multi_star) k_tiles<true><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap);
-    else k_tiles<false><<<nb, kTileThreads, 0, stream>>>(st, s, tl, nleaves, cap);
+    if (group == 4) launch_tiles_g<4>(st, s, tl, nleaves, multi_star, cap, stream);
+    else if (group == 2) launch_tiles_g<2>(st, s, tl, nleaves, multi_star, cap, stream);
+    else launch_tiles_g<1>(st, s, tl, nleaves, multi_star, cap, stream);
 }
 
 void launch_tiles(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
                   int multi_star, int cap, int density, const DevEos &eos, const DevMetric &g,
-                  const DevRates &out, cudaStream_t stream, int *nlaunch, int screen_lanes)
+                  const DevRates &out, cudaStream_t stream, int *nlaunch, int screen_lanes,
+                  int group)
 {
     if (nleaves <= 0) return;
-    launch_tiles_build(st, s, tl, nleaves, multi_star, cap, stream);
+    launch_tiles_build(st, s, tl, nleaves, multi_star, cap, stream, group);
     launch_screen(st, s, cap, density, eos, g, out, stream, screen_lanes);
     if (nlaunch) *nlaunch += 2;
 }

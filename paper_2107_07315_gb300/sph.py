@@ -95,7 +95,8 @@ class sph_options(C.Structure):
     _fields_ = [("h_nmin", C.c_int32), ("h_nmax", C.c_int32), ("max_neighbors", C.c_int32),
                 ("lanes_per_particle", C.c_int32), ("use_graph", C.c_int32),
                 ("totals_every", C.c_int32), ("sort_every", C.c_int32), ("skin", C.c_double),
-                ("screen_lanes", C.c_int32), ("persistent", C.c_int32)]
+                ("screen_lanes", C.c_int32), ("persistent", C.c_int32),
+                ("search_leaves", C.c_int32)]
 
 
 _lib = None
@@ -295,7 +296,7 @@ def sph_init(particles: dict, eos: dict, material: dict, metric=None, precision=
                         int(options.get("lanes_per_particle", 0)), int(options.get("use_graph", 1)),
                         int(options.get("totals_every", 0)), int(options.get("sort_every", 0)),
                         float(options.get("skin", 0.0)), int(options.get("screen_lanes", 0)),
-                        int(options.get("persistent", 0)))
+                        int(options.get("persistent", 0)), int(options.get("search_leaves", 0)))
     if stream is None:
         import torch
 

@@ -46,14 +46,16 @@ def test_roofline_entries():
 def test_launch_shape_record():
     b = _bench()
     st = [0] * 32
-    st[7], st[19], st[20] = 4, 8, 1
+    st[7], st[19], st[20], st[31] = 4, 8, 1, 2
+    st[28:31] = [90000, 80000, 85000]
     st[21:25] = [50000, 40000, 30000, 45000]  # ns: screen 4/8, pairs 4/8
     sh = b.launch_shape(st)
     assert sh["screen_lanes"] == 8 and sh["pair_lanes"] == 4 and sh["source"] == "autotuned"
+    assert sh["search_leaf_particles"] == 16 and sh["tuner_us_build"]["leaf_16"] == pytest.approx(80.0)
     assert sh["tuner_us_per_launch"]["screen_8"] == pytest.approx(40.0)
     # fixed default (screen 4, pairs 8) against the chosen (screen 8, pairs 4)
     assert sh["tuned_vs_fixed"] == pytest.approx((50000 + 45000) / (40000 + 30000))
-    st[20], st[21:25] = 0, [0, 0, 0, 0]
+    st[20], st[21:25], st[28:31] = 0, [0, 0, 0, 0], [0, 0, 0]
     sh = b.launch_shape(st)
     assert sh["source"] == "fixed" and "tuned_vs_fixed" not in sh
 

@@ -227,6 +227,8 @@ def test_autotuned_shape_matches_and_is_cached():
     stats = sph.sph_stats(ctx)
     assert stats[7] in (4, 8) and stats[19] in (4, 8)
     assert stats[20] == 1 and np.all(stats[21:25] > 0)
+    # the search leaf of the candidate build was timed too
+    assert np.all(stats[28:31] > 0) and stats[31] in (1, 2, 4)
     # the faster of each pair was kept
     assert stats[19] == (8 if stats[22] < stats[21] else 4)
     assert stats[7] == (8 if stats[24] < stats[23] else 4)
@@ -235,7 +237,7 @@ def test_autotuned_shape_matches_and_is_cached():
     assert_close(g, o, TOL_MIXED, label="autotune")
     g2, ctx2, _ = gpu_rhs(st, eos, MAT, None, sph.SPH_MIXED, dict(lanes_per_particle=-1))
     s2 = sph.sph_stats(ctx2)
-    assert s2[20] == 2 and s2[7] == stats[7] and s2[19] == stats[19]
+    assert s2[20] == 2 and s2[7] == stats[7] and s2[19] == stats[19] and s2[31] == stats[31]
     assert np.array_equal(s2[21:25], stats[21:25])
     # same shape, same order of sums: the same rates bit for bit
     for k in ("ax", "ay", "az", "dudt", "D"):

@@ -64,3 +64,34 @@ def test_displacement_test_rebuilds_and_lists_stay_exact():
     offs, idx = sph.neighbors(ctx)
     o_offs, o_idx = oracle.neighbors(g)
     assert np.array_equal(offs, o_offs) and np.array_equal(idx, o_idx)
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_search_leaf_size_changes_no_candidate(multi):
+    # a walk shared by 1, 2 or 4 tree leaves yields the same candidate leaves
+    # for every leaf (the (leaf, leaf) tile count is the same) and so the same
+    # lists and rates, bit for bit; several stars put stars' last and first
+    # leaves in one walk
+    if multi:
+        st, eos, met, _ = I.ensemble_state(nstars=6, seed=2107, scale_n=0.02, nr=512)
+    else:
+        st, eos, met, _ = I.star_state(20000, seed=4, amp_l0=1e-2, amp_l2=1e-2)
+    res = []
+    for g in (1, 2, 4):
+        dev = sph.device_state(st)
+        torch.cuda.synchronize()
+        ctx = sph.sph_init(dev, eos, MAT, met, sph.SPH_MIXED, dict(search_leaves=g),
+                           stream=stream().cuda_stream)
+        rates = sph.alloc_rates(len(st["x"]))
+        torch.cuda.synchronize()
+        sph.sph_rhs(ctx, rates)
+        sph.sph_sync(ctx)
+        stats = sph.sph_stats(ctx)
+        assert stats[31] == g
+        res.append((sph.to_numpy(rates), int(stats[16]), sph.neighbors(ctx)))
+        sph.sph_free(ctx)
+    for r, tiles, (offs, idx) in res[1:]:
+        assert tiles == res[0][1]
+        assert np.array_equal(offs, res[0][2][0]) and np.array_equal(idx, res[0][2][1])
+        for k in ("ax", "ay", "az", "dudt", "D", "rho", "dS", "ncount"):
+            assert np.array_equal(r[k], res[0][0][k]), k
