@@ -734,6 +734,9 @@ def campaign(args):
             ser[name] = (rho, q)
             res[name] = {"omega_radial": _fit_omega(t, rho), "omega_quadrupole": _fit_omega(t, q),
                          "ms_per_step": ms, "pairs_per_step": int(stats[0])}
+        if args.campaign_out:
+            np.savez(args.campaign_out, t=t, rho_mixed=ser["mixed"][0], qzz_mixed=ser["mixed"][1],
+                     rho_fp64=ser["fp64"][0], qzz_fp64=ser["fp64"][1])
         # how closely the two runs' series agree, against each series' swing
         for j, key in ((0, "core_density"), (1, "qzz")):
             a, b = ser["mixed"][j], ser["fp64"][j]
@@ -799,9 +802,19 @@ def campaign(args):
             torch.cuda.synchronize()
             ctx = sph.sph_init(d, eos, I.DEFAULT_MATERIAL, met, prec, opts,
                                stream=stream.cuda_stream)
+            # host-side retry: the state is saved every `every` steps; when
+            # the lists overflow (ejecta of the strong forcing grow h, and
+            # dense particles near them collect several hundred neighbours
+            # through h_a + h_b) the run goes back to the last save, doubles
+            # max_neighbors and steps again
+            every, cap, grown = 10 * chunk, 256, []
             ms, done, err = 0.0, 0, None
-            for k in range(0, steps, chunk):
-                if name == "fp64":
+            blob, blob_at = sph.sph_get_state(ctx), 0
+            k = 0
+            while k < steps:
+                if k % every == 0 and k != blob_at:
+                    blob, blob_at = sph.sph_get_state(ctx), k
+                if len(dts) <= k // chunk:
                     dts.append(_cfl_dt_device(d, eos))
                 dt = dts[k // chunk]
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -812,14 +825,23 @@ def campaign(args):
                 try:
                     sph.sph_sync(ctx)
                 except sph.SphError as e:
+                    if e.status == 4 and cap < 1024:
+                        cap *= 2
+                        grown.append({"at_step": k, "max_neighbors": cap})
+                        sph.sph_set_state(ctx, blob)
+                        sph.sph_set_max_neighbors(ctx, cap)
+                        k = blob_at
+                        continue
                     err = str(e)
                     break
                 torch.cuda.synchronize()
                 ms += e0.elapsed_time(e1)
-                done = k + min(chunk, steps - k)
+                k += min(chunk, steps - k)
+                done = k
             f = d["flags"].cpu().numpy()
             flags[name] = f
             out[name] = {"steps_done": done, "error": err, "ms_per_step": ms / max(done, 1),
+                         "capacity_retries": grown,
                          "yielded": int(((f & 1) != 0).sum()), "broken": int(((f & 2) != 0).sum())}
             sph.sph_free(ctx)
             del d
@@ -1081,6 +1103,8 @@ def main():
                     help="full-length paper-scale run instead of the benchmark line")
     ap.add_argument("--campaign-steps", type=int, default=0,
                     help="steps of the campaign (0: the configuration's own count)")
+    ap.add_argument("--campaign-out", default="",
+                    help="star1e6 campaign: also write the sampled series to this .npz file")
     ap.add_argument("--oracle-steps", type=int, default=200,
                     help="steps of the 2e4-particle oracle comparison in the crust4e6 campaign")
     ap.add_argument("--nstars", type=int, default=64)

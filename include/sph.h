@@ -136,8 +136,10 @@ typedef struct {
 /* Run options (host); NULL in sph_init means the defaults in brackets.
  * h_nmin, h_nmax: after each step multiply h by 1.0625 when the neighbour
  * count is below h_nmin and by 0.9375 above h_nmax [0, 0: off].
- * max_neighbors: most neighbours a particle may have (1..256); more raise
- * SPH_ERR_CAPACITY at sph_sync [0: 256].
+ * max_neighbors: most neighbours a particle may have (1..1024; the
+ * candidate list of a particle, every pair within (1 + skin)(h_a + h_b),
+ * must fit too); more raise SPH_ERR_CAPACITY at sph_sync.  The context
+ * holds two int32 lists of this length per particle [0: 256].
  * lanes_per_particle: 4 or 8 threads share one particle's list in the pair
  * kernels [0: 8]; -1 turns on the autotuner of the lane counts: sph_init evaluates one
  * right-hand side on the bound state (writing the rates), then times the
@@ -231,6 +233,35 @@ sph_status sph_sync(sph_ctx *ctx);
  * step without a curve sort).  Library service, no counterpart in the
  * paper.  Synchronous.  Errors: SPH_ERR_ARG (NULL ctx), SPH_ERR_CUDA. */
 sph_status sph_set_wait_limit(sph_ctx *ctx, int32_t polls);
+
+/* Change the list capacity per particle (max_neighbors, 1..1024) of a live
+ * context: the candidate and exact lists are allocated again at the new
+ * length (the old ones freed), the step graphs are captured again and the
+ * next right-hand side builds the candidate lists again.  With
+ * sph_get_state / sph_set_state this is the host-side retry after
+ * SPH_ERR_CAPACITY: restore the state saved before the failed steps, grow
+ * the capacity, step again; the result equals a run with the larger capacity
+ * from the start.  Library service, no counterpart in the paper.
+ * Synchronous.  Errors: SPH_ERR_ARG, SPH_ERR_OOM (the old lists are kept),
+ * SPH_ERR_CUDA. */
+sph_status sph_set_max_neighbors(sph_ctx *ctx, int32_t max_neighbors);
+
+/* Bounds-checked builds (libsph_checked.so, compiled with -DSPH_CHECKED):
+ * every list entry and permutation entry is tested against the particle
+ * range before it is used for an access; one outside raises a device error
+ * flag, the access goes to an index in range, and sph_sync reports
+ * SPH_ERR_BOUNDS.  sph_build_checked returns 1 in such a build, 0 otherwise.
+ * Library service (SURVEY's sanitizer substitute), no counterpart in the
+ * paper. */
+int32_t sph_build_checked(void);
+
+/* Checked builds only (SPH_ERR_ARG otherwise): overwrite entry k of the
+ * candidate list of sorted slot `slot` with `value`, to exercise the bounds
+ * check from the host.  The next right-hand side that reuses the candidate
+ * lists (no curve sort and no rebuild) reads it.  Synchronous.  Errors:
+ * SPH_ERR_ARG (NULL ctx, slot or k out of range, unchecked build),
+ * SPH_ERR_CUDA. */
+sph_status sph_checked_set_candidate(sph_ctx *ctx, int64_t slot, int32_t k, int32_t value);
 
 /* Neighbour lists of the last right-hand side, CSR in caller order with
  * ascending caller indices (b in N(a) iff b != a, same star and

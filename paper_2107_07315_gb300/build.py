@@ -16,6 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
+# bounds-checked variant (-DSPH_CHECKED): list and permutation entries tested
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libsph_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sph_build.cu", "sph_tiles.cu", "sph_pairs.cu", "sph_step.cu", "sph_api.cu",
            "sph_noalloc.cu", "sph_peak.cu"]
@@ -40,16 +43,21 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
+def build(verbose: bool = False, extra_flags=(), force: bool = False,
+          checked: bool = False) -> str:
+    """Compile the library (checked: the bounds-checked variant)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if checked:
+        extra_flags = list(extra_flags) + ["-DSPH_CHECKED"]
+    os.makedirs(bdir, exist_ok=True)
     header_deps = [os.path.join(CSRC, "sph_internal.cuh"), os.path.join(CSRC, "sph_device.cuh"),
                    os.path.join(CSRC, "sph_screen.cuh"), os.path.join(ROOT, "include", "sph.h")]
     jobs = []
     objs = []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [path] + header_deps):
             jobs.append([nvcc] + _flags(extra_flags) + ["-c", path, "-o", obj])
@@ -64,14 +72,14 @@ def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp.%d" % os.getpid()
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
 
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, checked="--checked" in sys.argv))

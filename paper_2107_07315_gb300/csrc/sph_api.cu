@@ -13,6 +13,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sph_internal.cuh"
 
 using namespace sph;
@@ -29,6 +31,15 @@ sph_status fail(sph_status st, const char *fmt, ...)
     va_end(ap);
     return st;
 }
+
+// NVTX range around a host entry point (a profiler shows the library's calls
+// on its timeline; without a tool attached the calls return at once).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define CUDA_TRY(call)                                                                   \
     do {                                                                                 \
@@ -437,6 +448,7 @@ sph_status time_stage(sph_ctx *c, cudaEvent_t e0, cudaEvent_t e1, int64_t *ns,
 
 sph_status autotune_shape(sph_ctx *c, bool lanes, bool persist)
 {
+    NvtxRange nvtx_("sph_autotune");
     const bool fp64 = c->prec == SPH_FP64;
     persist = persist && !fp64;
     const int code = (lanes ? 1 : 0) | (persist ? 2 : 0) |
@@ -484,13 +496,14 @@ sph_status autotune_shape(sph_ctx *c, bool lanes, bool persist)
             c->screen_lanes = c->tune_ns[1] < c->tune_ns[0] ? 8 : 4;
             c->lanes = c->tune_ns[3] < c->tune_ns[2] ? 8 : 4;
         }
-        // candidate builds (the rebuild flag set before each launch)
+        // candidate builds (the rebuild flag set before each launch); above
+        // the default list capacity the walk has one shape only
         const int groups[3] = {1, 2, 4};
         const int caps[3] = {kCandCap, 2 * kCandCap, 2 * kCandCap};
         static const int one = 1;
         int best = 1;
         int64_t best_ns = 0;
-        for (int k = 0; k < 3 && rc == SPH_OK; ++k) {
+        for (int k = 0; k < (c->cap > kRowCapDefault ? 1 : 3) && rc == SPH_OK; ++k) {
             const int gk = groups[k];
             rc = time_stage(c, e0, e1, &c->tune_ns[6 + k], [&] {
                 cudaMemcpyAsync(&c->s.sc->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice,
@@ -548,6 +561,13 @@ sph_status autotune_shape(sph_ctx *c, bool lanes, bool persist)
     return SPH_OK;
 }
 
+// Candidate leaves one tile-search walk holds (sph_tiles.cu TileShape).
+int walk_capacity(const sph_ctx *c)
+{
+    if (c->cap > kRowCapDefault) return 4 * kCandCap;
+    return c->group > 1 ? 2 * kCandCap : kCandCap;
+}
+
 void drop_graph(sph_ctx *c, int k)
 {
     if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
@@ -571,6 +591,7 @@ bool resort_at(const sph_ctx *c, int64_t k)
 
 sph_status capture_step(sph_ctx *c, double dt, bool resort)
 {
+    NvtxRange nvtx_("sph_capture_step");
     const int g = resort ? 1 : 0;
     drop_graph(c, g);
     cudaGraph_t graph = nullptr;
@@ -692,7 +713,7 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
         c->opt = sph_options{};
         c->opt.use_graph = 1;
     }
-    c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : kRowCap;
+    c->cap = c->opt.max_neighbors > 0 ? c->opt.max_neighbors : kRowCapDefault;
     c->lanes = c->opt.lanes_per_particle > 0 ? c->opt.lanes_per_particle : 8;
     c->screen_lanes = c->opt.screen_lanes > 0 ? c->opt.screen_lanes : 4;
     c->group = c->opt.search_leaves > 0 ? c->opt.search_leaves : 1;
@@ -927,6 +948,7 @@ sph_status sph_init(sph_ctx **out, const sph_particles *particles, const sph_eos
                     const sph_material *material, const sph_metric *metric,
                     sph_precision precision, const sph_options *options, void *cuda_stream)
 {
+    NvtxRange nvtx_("sph_init");
     g_err[0] = 0;
     if (!out) return fail(SPH_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -954,6 +976,7 @@ sph_status sph_init(sph_ctx **out, const sph_particles *particles, const sph_eos
 
 sph_status sph_rhs(sph_ctx *c, const sph_rates *out)
 {
+    NvtxRange nvtx_("sph_rhs");
     if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
     if (c->n > 0 && (!out->ax || !out->ay || !out->az || !out->dudt || !out->drhodt || !out->rho ||
                      !out->P || !out->D || !out->cs || !out->deps || !out->dR || !out->dS ||
@@ -973,6 +996,7 @@ sph_status sph_rhs(sph_ctx *c, const sph_rates *out)
 
 sph_status sph_step(sph_ctx *c, double dt, int32_t nsteps)
 {
+    NvtxRange nvtx_("sph_step");
     if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(SPH_ERR_ARG, "bad dt or nsteps");
     if (c->n == 0) {
@@ -1026,6 +1050,7 @@ sph_status sph_step(sph_ctx *c, double dt, int32_t nsteps)
 
 sph_status sph_sync(sph_ctx *c)
 {
+    NvtxRange nvtx_("sph_sync");
     if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->n == 0) return SPH_OK;
@@ -1044,7 +1069,7 @@ sph_status sph_sync(sph_ctx *c)
             return fail(SPH_ERR_CAPACITY,
                         "a particle has more than max_neighbors = %d neighbours, or a "
                         "tile-search walk more than %d candidate leaves",
-                        c->cap, c->group > 1 ? 2 * kCandCap : kCandCap);
+                        c->cap, walk_capacity(c));
         if (err & ERR_BOUNDS) return fail(SPH_ERR_BOUNDS, "index out of bounds");
     }
     return SPH_OK;
@@ -1061,8 +1086,80 @@ sph_status sph_set_wait_limit(sph_ctx *c, int32_t polls)
     return SPH_OK;
 }
 
+sph_status sph_set_max_neighbors(sph_ctx *c, int32_t max_neighbors)
+{
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    if (max_neighbors < 1 || max_neighbors > kRowCap)
+        return fail(SPH_ERR_ARG, "max_neighbors must be 1..%d", kRowCap);
+    if (c->n == 0 || max_neighbors == c->cap) {
+        c->cap = max_neighbors;
+        c->opt.max_neighbors = max_neighbors;
+        return SPH_OK;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->side) CUDA_TRY(cudaStreamSynchronize(c->side));
+    const size_t count = (size_t)c->n * max_neighbors;
+    int32_t *vl = nullptr, *nb = nullptr;
+    cudaError_t e = cudaMalloc((void **)&vl, count * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&nb, count * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        if (vl) cudaFree(vl);
+        cudaGetLastError();
+        return fail(SPH_ERR_OOM, "lists of %d entries per particle: %s", max_neighbors,
+                    cudaGetErrorString(e));
+    }
+    for (void *&p : c->allocs) {
+        if (p == (void *)c->s.vlist) {
+            cudaFree(p);
+            p = vl;
+        } else if (p == (void *)c->s.nbr) {
+            cudaFree(p);
+            p = nb;
+        }
+    }
+    c->s.vlist = vl;
+    c->s.nbr = nb;
+    c->cap = max_neighbors;
+    c->opt.max_neighbors = max_neighbors;
+    // the step graphs hold the old lists and capacity; the next right-hand
+    // side builds the candidate lists again
+    drop_graph(c);
+    const int zero = 0;
+    CUDA_TRY(cudaMemcpy(&c->s.sc->built, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    return SPH_OK;
+}
+
+int32_t sph_build_checked(void)
+{
+#ifdef SPH_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+sph_status sph_checked_set_candidate(sph_ctx *c, int64_t slot, int32_t k, int32_t value)
+{
+#ifdef SPH_CHECKED
+    if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+    if (slot < 0 || slot >= c->n || k < 0 || k >= c->cap)
+        return fail(SPH_ERR_ARG, "slot or entry out of range");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaMemcpy(c->s.vlist + slot * (int64_t)c->cap + k, &value, sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+    return SPH_OK;
+#else
+    (void)c;
+    (void)slot;
+    (void)k;
+    (void)value;
+    return fail(SPH_ERR_ARG, "sph_checked_set_candidate exists only in bounds-checked builds");
+#endif
+}
+
 sph_status sph_neighbors(sph_ctx *c, int64_t *offsets, int32_t *idx, int64_t cap)
 {
+    NvtxRange nvtx_("sph_neighbors");
     if (!c || !offsets || (cap > 0 && !idx) || cap < 0) return fail(SPH_ERR_ARG, "bad argument");
     const int64_t n = c->n;
     CUDA_TRY(cudaMemsetAsync(offsets, 0, (n + 1) * sizeof(int64_t), c->stream));
@@ -1168,6 +1265,7 @@ sph_status sph_relax_finish(sph_ctx *c, const sph_eos *eos)
 
 sph_status sph_totals(sph_ctx *c, double out[16])
 {
+    NvtxRange nvtx_("sph_totals");
     if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
     StepState ss = step_state_of(c);
     launch_totals(ss, c->have_rates ? c->r.ncount : nullptr, c->tot_partial, c->tot_out, c->stream);
@@ -1178,6 +1276,7 @@ sph_status sph_totals(sph_ctx *c, double out[16])
 
 sph_status sph_totals_per_star(sph_ctx *c, double *out, int32_t nstars)
 {
+    NvtxRange nvtx_("sph_totals_per_star");
     if (!c || !out) return fail(SPH_ERR_ARG, "null argument");
     if (nstars != c->nstars)
         return fail(SPH_ERR_ARG, "nstars = %d, the context holds %d stars", nstars, c->nstars);

@@ -383,6 +383,22 @@ __device__ __forceinline__ bool order_invalid(const DevScalars *sc)
     return (*(volatile const int *)&sc->err & ERR_TIMEOUT) != 0;
 }
 
+// A data-dependent index (a list entry or a permutation entry) about to be
+// used for an access.  Bounds-checked builds (-DSPH_CHECKED) test
+// 0 <= j < n and, outside, raise ERR_BOUNDS and return 0, an index in range,
+// so the access stays in bounds and sph_sync reports SPH_ERR_BOUNDS.  Other
+// builds return j unchanged.
+#ifdef SPH_CHECKED
+__device__ __forceinline__ int checked_index(int j, int64_t n, DevScalars *sc)
+{
+    if (j >= 0 && (int64_t)j < n) return j;
+    atomicOr(&sc->err, ERR_BOUNDS);
+    return 0;
+}
+#else
+__device__ __forceinline__ int checked_index(int j, int64_t, DevScalars *) { return j; }
+#endif
+
 constexpr int kSpinLimit = 1 << 22;  // default polls of a device-side wait before giving up
 
 // Polls a device-side wait may make (DevScalars::spin_limit: 0 the default,

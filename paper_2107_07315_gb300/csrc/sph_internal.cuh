@@ -47,7 +47,8 @@ constexpr int kMaxLevels = 16;
 constexpr int kTreeBlock = 64;    // leaves per block in the tree kernel (8^2)
 constexpr int kTreeBlockLevels = 2;
 constexpr int kCandCap = 256;     // candidate leaves per leaf (pair tiles per leaf)
-constexpr int kRowCap = 256;      // most neighbours per particle (list capacity limit)
+constexpr int kRowCap = 1024;     // largest max_neighbors (list capacity per particle)
+constexpr int kRowCapDefault = 256;  // list capacity per particle when max_neighbors is 0
 
 // Device error word bits.
 enum : int {
@@ -276,7 +277,9 @@ void launch_screen(const DevState &st, const Scratch &s, int cap, int density,
 // Candidate-list build alone (the kernel returns at once unless the tree
 // kernel asked for a rebuild).
 // group: tree leaves per tile-search walk (1, 2 or 4: a search leaf of 8, 16
-// or 32 particles; the candidate lists are the same for each).
+// or 32 particles; the candidate lists are the same for each).  With a list
+// capacity above kRowCapDefault the walk takes one tree leaf and holds 1024
+// candidate leaves (group is ignored).
 void launch_tiles_build(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
                         int multi_star, int cap, cudaStream_t stream, int group = 1);
 

@@ -63,7 +63,7 @@ k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRa
         double sum = 0.0;
         const int32_t *list = s.nbr + i * (int64_t)cap;
         for (int k = sub; k < cnt; k += LPI) {
-            int j = list[k];
+            int j = checked_index(list[k], n, s.sc);
             double4_32a q0 = s.rec64[(int64_t)j * 3 + 0];
             double mj = s.rec64[(int64_t)j * 3 + 1].x;
             double dx = a0.x - q0.x, dy = a0.y - q0.y, dz = a0.z - q0.z;
@@ -95,7 +95,7 @@ k_density_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMetric g, DevRa
     const double D = s_D[threadIdx.x];
     const double4_32a a0 = s.rec64[i * 3 + 0];
     const double mi = s.rec64[i * 3 + 1].x;
-    const int c = s.perm[i];
+    const int c = checked_index(s.perm[i], n, s.sc);
     const int star = st.star ? st.star[c] : 0;
     const double vx = st.vx[c], vy = st.vy[c], vz = st.vz[c];
     const PosD pos{a0.x, a0.y, a0.z};
@@ -178,10 +178,10 @@ __device__ __forceinline__ void force_block(int64_t n, const DevState &st, const
         float G00 = 0.f, G01 = 0.f, G02 = 0.f, G10 = 0.f, G11 = 0.f, G12 = 0.f, G20 = 0.f,
               G21 = 0.f, G22 = 0.f;
         const int32_t *list = s.nbr + i * (int64_t)cap;
-        int jn = sub < cnt ? list[sub] : 0;
+        int jn = sub < cnt ? checked_index(list[sub], n, s.sc) : 0;
         for (int k = sub; k < cnt; k += LPI) {
             const int j = jn;
-            if (k + LPI < cnt) jn = list[k + LPI];
+            if (k + LPI < cnt) jn = checked_index(list[k + LPI], n, s.sc);
             const float4 q0 = s.rec[j], q1 = s.rec[n + j];
             const float4 q2 = s.rec[2 * n + j], q3 = s.rec[3 * n + j];
             const bool solid_j = q3.w != 0.f;  // type rides in the record: no extra load
@@ -255,7 +255,7 @@ __device__ __forceinline__ void force_block(int64_t n, const DevState &st, const
     const int64_t i = base + threadIdx.x;
     if (threadIdx.x >= PB || i >= n) return;
     const int t = threadIdx.x;
-    const int c = s.perm[i];
+    const int c = checked_index(s.perm[i], n, s.sc);
     const int star = st.star ? st.star[c] : 0;
     const float4 a0 = s.rec[i], a1 = s.rec[n + i];
     const float4 a2 = s.rec[2 * n + i];
@@ -318,7 +318,7 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
         double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         const int32_t *list = s.nbr + i * (int64_t)cap;
         for (int k = sub; k < cnt; k += LPI) {
-            const int j = list[k];
+            const int j = checked_index(list[k], n, s.sc);
             const double4_32a q0 = s.rec64[(int64_t)j * 3 + 0], q1 = s.rec64[(int64_t)j * 3 + 1];
             const double4_32a q2 = s.rec64[(int64_t)j * 3 + 2];
             const bool solid_j = s.tys[j] == 1;
@@ -391,7 +391,7 @@ k_force_fp64(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat, Dev
     const int64_t i = base + threadIdx.x;
     if (threadIdx.x >= PB || i >= n) return;
     const int t = threadIdx.x;
-    const int c = s.perm[i];
+    const int c = checked_index(s.perm[i], n, s.sc);
     const int star = st.star ? st.star[c] : 0;
     const double4_32a a0 = s.rec64[i * 3 + 0], a1 = s.rec64[i * 3 + 1], a2 = s.rec64[i * 3 + 2];
     const double *pp = s.pp64 + i * 8;

@@ -56,9 +56,9 @@ __device__ __forceinline__ void screen_block(const DevState &st, const Scratch &
     // drops it).  The records of the next candidate are loaded one iteration
     // ahead, its index two ahead, so two gathers per lane are in flight.
     const int vmax = __reduce_max_sync(0xffffffffu, vc);
-    int jn = sub < vc ? vl[sub] : 0;
+    int jn = sub < vc ? checked_index(vl[sub], n, sc) : 0;
     float4 n0 = s.rec[jn], n1 = s.rec[n + jn];
-    int jnn = sub + LPI < vc ? vl[sub + LPI] : 0;
+    int jnn = sub + LPI < vc ? checked_index(vl[sub + LPI], n, sc) : 0;
     for (int k0 = 0; k0 < vmax; k0 += LPI) {
         const int k = k0 + sub;
         const bool kv = k < vc;
@@ -69,7 +69,7 @@ __device__ __forceinline__ void screen_block(const DevState &st, const Scratch &
             n0 = s.rec[jn];
             n1 = s.rec[n + jn];
         }
-        jnn = k + 2 * LPI < vc ? vl[k + 2 * LPI] : 0;
+        jnn = k + 2 * LPI < vc ? checked_index(vl[k + 2 * LPI], n, sc) : 0;
         const float dx = (a0.x - b0.x) + (a1.x - b1.x);
         const float dy = (a0.y - b0.y) + (a1.y - b1.y);
         const float dz = (a0.z - b0.z) + (a1.z - b1.z);
@@ -159,7 +159,7 @@ __device__ __forceinline__ void screen_block(const DevState &st, const Scratch &
     // equation of state of particle i
     const float hi = a0.w;
     const float D = a1.w * kInvPiF / (hi * hi * hi) + (sum - comp);
-    const int c = s.perm[i];
+    const int c = checked_index(s.perm[i], n, sc);
     const int star = st.star ? st.star[c] : 0;
     const float vx = f64_to_f32_rn(st.vx[c]), vy = f64_to_f32_rn(st.vy[c]),
                 vz = f64_to_f32_rn(st.vz[c]);

@@ -74,8 +74,16 @@ constexpr int kChunk = 4;  // candidate leaves staged per chunk (32 particles)
 // particles) share one walk, whose front holds at most kCap candidate
 // leaves; kWarps warps per block (one walk per warp).  The candidate lists
 // are the same for every G (see k_tiles); G sets only the cost of a build.
-template <int G>
+// BIG (list capacity above the default 256): one tree leaf per walk and a
+// front of 1024 candidate leaves, one warp per block, for particles whose h
+// is many times their neighbours' (the ejecta of a strongly driven star).
+template <int G, bool BIG = false>
 struct TileShape;
+template <>
+struct TileShape<1, true> {
+    static constexpr int kWarps = 1, kCap = 4 * kCandCap, kMinBlocks = 8;
+    using Reach = unsigned char;
+};
 template <>
 struct TileShape<1> {
     static constexpr int kWarps = 4, kCap = kCandCap, kMinBlocks = 8;
@@ -101,12 +109,12 @@ struct TileShape<4> {
 // (q lies in A's box, and every ancestor of B has a larger box and h_max),
 // and both tests pass exactly the same pairs, so the candidate lists do not
 // depend on G.
-template <bool MULTI_STAR, int G>
-__global__ void __launch_bounds__(32 * TileShape<G>::kWarps, TileShape<G>::kMinBlocks)
+template <bool MULTI_STAR, int G, bool BIG>
+__global__ void __launch_bounds__(32 * TileShape<G, BIG>::kWarps, TileShape<G, BIG>::kMinBlocks)
 k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
 {
-    constexpr int W = TileShape<G>::kWarps, CAP = TileShape<G>::kCap, NP = kLeaf * G;
-    using Reach = typename TileShape<G>::Reach;
+    constexpr int W = TileShape<G, BIG>::kWarps, CAP = TileShape<G, BIG>::kCap, NP = kLeaf * G;
+    using Reach = typename TileShape<G, BIG>::Reach;
     __shared__ int s_front[W][2][CAP];
     __shared__ Reach s_reach[W][2][CAP];
     __shared__ float4 s_p[W][NP];        // the group's fl32 positions and h (walk)
@@ -443,21 +451,22 @@ void launch_screen(const DevState &st, const Scratch &s, int cap, int density,
     }
 }
 
-template <int G>
+template <int G, bool BIG = false>
 static void launch_tiles_g(const DevState &st, const Scratch &s, const TreeLevels &tl,
                            int nleaves, int multi_star, int cap, cudaStream_t stream)
 {
-    constexpr int W = TileShape<G>::kWarps;
+    constexpr int W = TileShape<G, BIG>::kWarps;
     const int nb = (nleaves + W * G - 1) / (W * G);
-    if (multi_star) k_tiles<true, G><<<nb, 32 * W, 0, stream>>>(st, s, tl, nleaves, cap);
-    else k_tiles<false, G><<<nb, 32 * W, 0, stream>>>(st, s, tl, nleaves, cap);
+    if (multi_star) k_tiles<true, G, BIG><<<nb, 32 * W, 0, stream>>>(st, s, tl, nleaves, cap);
+    else k_tiles<false, G, BIG><<<nb, 32 * W, 0, stream>>>(st, s, tl, nleaves, cap);
 }
 
 void launch_tiles_build(const DevState &st, const Scratch &s, const TreeLevels &tl, int nleaves,
                         int multi_star, int cap, cudaStream_t stream, int group)
 {
     if (nleaves <= 0) return;
-    if (group == 4) launch_tiles_g<4>(st, s, tl, nleaves, multi_star, cap, stream);
+    if (cap > kRowCapDefault) launch_tiles_g<1, true>(st, s, tl, nleaves, multi_star, cap, stream);
+    else if (group == 4) launch_tiles_g<4>(st, s, tl, nleaves, multi_star, cap, stream);
     else if (group == 2) launch_tiles_g<2>(st, s, tl, nleaves, multi_star, cap, stream);
     else launch_tiles_g<1>(st, s, tl, nleaves, multi_star, cap, stream);
 }

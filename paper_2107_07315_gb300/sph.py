@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsph.so")
+# SPH_CHECKED=1 in the environment selects the bounds-checked build
+LIB_PATH = os.path.join(_HERE, "libsph_checked.so" if os.environ.get("SPH_CHECKED") == "1"
+                        else "libsph.so")
 
 SPH_FP64 = 0
 SPH_MIXED = 1
@@ -28,7 +30,8 @@ EXPORTS = ("sph_init", "sph_rhs", "sph_step", "sph_sync", "sph_neighbors", "sph_
            "sph_stats", "sph_timing", "sph_timing_read", "sph_state_size", "sph_get_state",
            "sph_set_state", "sph_free", "sph_last_error", "sph_neighbors_noalloc",
            "sph_set_external", "sph_relax_finish", "sph_set_wait_limit", "sph_peak_rates",
-           "sph_totals_per_star")
+           "sph_totals_per_star", "sph_build_checked", "sph_checked_set_candidate",
+           "sph_set_max_neighbors")
 
 
 class SphError(RuntimeError):
@@ -107,7 +110,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libsph.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            raise RuntimeError("%s is not built; run __graft_entry__.build()" % LIB_PATH)
         L = C.CDLL(LIB_PATH)
         vp = C.c_void_p
         L.sph_init.argtypes = [C.POINTER(vp), C.POINTER(sph_particles), C.POINTER(sph_eos),
@@ -133,6 +136,9 @@ def lib():
         L.sph_set_external.argtypes = [vp, C.POINTER(sph_external)]
         L.sph_relax_finish.argtypes = [vp, C.POINTER(sph_eos)]
         L.sph_last_error.restype = C.c_char_p
+        L.sph_build_checked.argtypes = []
+        L.sph_set_max_neighbors.argtypes = [vp, C.c_int32]
+        L.sph_checked_set_candidate.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32]
         for f in EXPORTS:
             if f not in ("sph_free", "sph_last_error"):
                 getattr(L, f).restype = C.c_int
@@ -348,6 +354,19 @@ def sph_peak_rates() -> dict:
     return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "sms": int(out[2])}
 
 
+def sph_set_max_neighbors(ctx: SphCtx, max_neighbors: int) -> None:
+    _check(lib().sph_set_max_neighbors(ctx.handle, int(max_neighbors)), "sph_set_max_neighbors")
+
+
+def sph_build_checked() -> bool:
+    return bool(lib().sph_build_checked())
+
+
+def sph_checked_set_candidate(ctx: SphCtx, slot: int, k: int, value: int) -> None:
+    _check(lib().sph_checked_set_candidate(ctx.handle, int(slot), int(k), int(value)),
+           "sph_checked_set_candidate")
+
+
 def sph_set_wait_limit(ctx: SphCtx, polls: int) -> None:
     _check(lib().sph_set_wait_limit(ctx.handle, int(polls)), "sph_set_wait_limit")
 
@@ -366,7 +385,8 @@ def sph_totals_per_star(ctx: SphCtx, nstars: int) -> np.ndarray:
     """FP64 totals of each star: array [nstars, 16] (columns as sph_totals)."""
     out = np.zeros((nstars, 16), np.float64)
     _check(lib().sph_totals_per_star(ctx.handle, out.ctypes.data_as(_d), int(nstars)),
-           "sph_totals_per_star")
+           "sph_totals_per_star", "sph_build_checked", "sph_checked_set_candidate",
+           "sph_set_max_neighbors")
     return out
 
 

@@ -85,3 +85,20 @@ def test_product_package_does_not_use_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
                 assert "liboracle" not in txt and "sph_oracle" not in txt, f
+
+
+def test_checked_build_exports_the_same_symbols_and_says_so(lib):
+    # the bounds-checked variant (-DSPH_CHECKED) has the same boundary; each
+    # build reports which one it is, and only the checked one accepts the
+    # candidate-list write that exercises its bounds check
+    from paper_2107_07315_gb300 import build
+
+    chk = ctypes.CDLL(build.build(checked=True))
+    for name in _declared():
+        assert hasattr(chk, name), name
+    chk.sph_build_checked.restype = ctypes.c_int32
+    lib.sph_build_checked.restype = ctypes.c_int32
+    assert chk.sph_build_checked() == 1 and lib.sph_build_checked() == 0
+    lib.sph_checked_set_candidate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_int32]
+    assert lib.sph_checked_set_candidate(None, 0, 0, 0) == 1

@@ -159,6 +159,57 @@ def test_capacity_error_is_reported():
     assert e.value.status == 4
 
 
+@pytest.mark.parametrize("prec,tol", PREC)
+def test_lists_beyond_the_default_capacity(prec, tol):
+    # ten particles with h raised 2.5x reach about 300 neighbours through
+    # h_a + h_b: the default capacity of 256 reports it, a context with
+    # max_neighbors = 600 holds the exact lists and rates
+    st, eos = I.random_state(3000, seed=41, vel=0.2, stress=0.05)
+    big = np.arange(0, 3000, 300)
+    st["h"][big] *= 2.5
+    o = oracle.rhs(st, eos, MAT, None, scales=True)
+    assert o["ncount"].max() > 256
+    dev = sph.device_state(st)
+    ctx = sph.sph_init(dev, eos, MAT, None, prec)
+    sph.sph_rhs(ctx, sph.alloc_rates(len(st["x"])))
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_sync(ctx)
+    assert e.value.status == 4
+    sph.sph_free(ctx)
+    _check(st, eos, prec=prec, tol=tol, options=dict(max_neighbors=600), label="cap 600")
+
+
+def test_capacity_retry_grows_the_lists():
+    # the host-side retry after SPH_ERR_CAPACITY: restore the checkpoint
+    # taken before the failed steps, grow max_neighbors, step again; the
+    # state equals a run with the larger capacity from the start
+    st, eos = I.random_state(3000, seed=41, vel=0.2, stress=0.05)
+    st["h"][np.arange(0, 3000, 300)] *= 2.5
+    dt = 0.2 * I.cfl_dt(st, eos)
+    dev = sph.device_state(st)
+    ctx = sph.sph_init(dev, eos, MAT, None, sph.SPH_MIXED, dict(sort_every=3))
+    blob = sph.sph_get_state(ctx)
+    sph.sph_step(ctx, dt, 4)
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_sync(ctx)
+    assert e.value.status == 4
+    sph.sph_set_state(ctx, blob)
+    sph.sph_set_max_neighbors(ctx, 600)
+    assert sph.sph_stats(ctx)[6] == 600
+    sph.sph_step(ctx, dt, 4)
+    sph.sph_sync(ctx)
+    a = sph.to_numpy(dev)
+    dev2 = sph.device_state(st)
+    ref = sph.sph_init(dev2, eos, MAT, None, sph.SPH_MIXED, dict(sort_every=3, max_neighbors=600))
+    sph.sph_step(ref, dt, 4)
+    sph.sph_sync(ref)
+    b = sph.to_numpy(dev2)
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "S", "flags"):
+        assert np.array_equal(a[k], b[k]), k
+    with pytest.raises(sph.SphError):
+        sph.sph_set_max_neighbors(ctx, 2000)
+
+
 def test_nonfinite_input_is_reported():
     st, eos, _, _ = I.cube_state(n_side=6)
     st["x"][3] = np.nan
