@@ -385,8 +385,7 @@ def sph_totals_per_star(ctx: SphCtx, nstars: int) -> np.ndarray:
     """FP64 totals of each star: array [nstars, 16] (columns as sph_totals)."""
     out = np.zeros((nstars, 16), np.float64)
     _check(lib().sph_totals_per_star(ctx.handle, out.ctypes.data_as(_d), int(nstars)),
-           "sph_totals_per_star", "sph_build_checked", "sph_checked_set_candidate",
-           "sph_set_max_neighbors")
+           "sph_totals_per_star")
     return out
 
 

@@ -102,3 +102,16 @@ def test_checked_build_exports_the_same_symbols_and_says_so(lib):
     lib.sph_checked_set_candidate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_int32]
     assert lib.sph_checked_set_candidate(None, 0, 0, 0) == 1
+
+
+def test_binding_wrappers_call_the_status_check_with_two_arguments():
+    # every wrapper passes (status, name) to _check; a stray argument would
+    # only surface on a GPU
+    import ast
+
+    src = open(os.path.join(ROOT, "paper_2107_07315_gb300", "sph.py")).read()
+    calls = [n for n in ast.walk(ast.parse(src))
+             if isinstance(n, ast.Call) and getattr(n.func, "id", None) == "_check"]
+    assert calls
+    for c in calls:
+        assert len(c.args) == 2 and not c.keywords, ast.unparse(c)
