@@ -778,6 +778,14 @@ sph_status init_impl(sph_ctx *c, const sph_particles *p, const sph_eos *eos,
     const int64_t nn = n > 0 ? n : 1;
     Scratch &s = c->s;
     STATUS_TRY(c->alloc(&s.perm, nn));
+    if (n > 0) {
+        // the identity until the first curve sort, so that a checkpoint taken
+        // before any step restores
+        std::vector<int32_t> ident((size_t)n);
+        for (int64_t i = 0; i < n; ++i) ident[(size_t)i] = (int32_t)i;
+        CUDA_TRY(cudaMemcpy(s.perm, ident.data(), (size_t)n * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+    }
     STATUS_TRY(c->alloc(&s.keys[0], nn));
     STATUS_TRY(c->alloc(&s.keys[1], nn));
     STATUS_TRY(c->alloc(&s.vals[0], nn));
@@ -1445,6 +1453,10 @@ sph_status sph_set_state(sph_ctx *c, const void *host_buf, int64_t bytes)
     STATUS_TRY(put(c->s.perm, 4 * (size_t)n));
     c->steps = hdr[2];
     c->have_rates = (int)hdr[3];
+    // the candidate lists belong to the order and positions of their own
+    // build, not to the restored ones: the next right-hand side builds them
+    const int zero = 0;
+    CUDA_TRY(cudaMemcpy(&c->s.sc->built, &zero, sizeof(int), cudaMemcpyHostToDevice));
     return SPH_OK;
 }
 

@@ -164,8 +164,7 @@ __global__ void k_bbox(DevState st, unsigned long long *partial, unsigned int *d
         sc->pairs_last = 0ull;
         sc->tree_done = 0;
         sc->max_count = 0;
-        sc->disp2_max = 0u;
-        sc->growth_max = 0u;
+        sc->q_max = 0u;
         sc->resorted = 0;
         sc->xmax_f = (float)m * 1.000001f;
         sc->pq_head = 0u;
@@ -514,27 +513,26 @@ __device__ __forceinline__ float4 node_merge_b(float4 a, float4 b)
 
 // Whether the candidate lists must be built again for this right-hand side
 // (the last block of the tree kernel decides, once every block has reduced
-// the displacements and h growth since the lists were built).  A pair within
-// h_a + h_b now was within (1 + g)(h_a0 + h_b0) + 2D when the lists were built
-// (g the largest relative growth of h, D the largest displacement), so lists
-// of every pair within (1 + eps)(h_a0 + h_b0) hold every neighbour while
-// 2D <= (eps - g) 2 h_min0.  D and g come from fl32 positions and h; the
-// margins cover their rounding (u |x| per coordinate, 3u per ratio).
+// q_a = d_a / h_a0 + g_a, d_a the displacement of particle a since the lists
+// were built, h_a0 its h then and g_a = h_a / h_a0 - 1).  A pair within
+// h_a + h_b now was within h_a + h_b + d_a + d_b <= (1 + q_a) h_a0 +
+// (1 + q_b) h_b0 <= (1 + max q)(h_a0 + h_b0) when the lists were built, so
+// lists of every pair within (1 + eps)(h_a0 + h_b0) hold every neighbour while
+// max q < eps.  q_a comes from fl32 positions and h with margins that make it
+// an upper bound (k_tree).
 __device__ void decide_rebuild(DevScalars *sc)
 {
     const float eps = sc->skin;
     bool rebuild = !sc->built || sc->resorted || !(eps >= 0.f);
     if (!rebuild) {
-        const float g = fmaxf(__uint_as_float(*(volatile unsigned *)&sc->growth_max), 0.f) + 4e-7f;
-        const float D = sqrtf(__uint_as_float(*(volatile unsigned *)&sc->disp2_max)) * 1.000001f +
-                        4.f * 5.9604645e-8f * sc->xmax_f;
-        rebuild = !(g < eps) || !(2.f * D <= (eps - g) * 2.f * sc->hmin_build * 0.999999f);
+        // NaN (lists never built for some slot) orders above every number
+        const float q = __uint_as_float(*(volatile unsigned *)&sc->q_max);
+        rebuild = !(q * 1.000001f < eps);
     }
     sc->rebuild = rebuild ? 1 : 0;
     if (rebuild) {
         sc->built = 1;
         sc->builds += 1ull;
-        sc->hmin_build = 3.0e38f;  // the build takes the minimum again
         sc->tiles_last = 0ull;
         sc->max_cand = 0;
     }
@@ -556,7 +554,13 @@ __global__ void k_tree(const float4 *pos4, const float4 *pos_build, const int32_
     const int l = blockIdx.x * kTreeBlock + t;
     const int nleaves = tl.count[0];
     float4 a = make_float4(3e38f, 3e38f, 3e38f, 0.f), b = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
-    float d2 = 0.f, gr = 0.f;
+    // q_a = d_a / h_a0 + g_a bounded from above: the fl32 displacement plus
+    // 4 u |x|_max for the rounding of both fl32 positions, divided by the
+    // fl32 h_a0 with a 1e-6 relative margin (the rounding of h_a0 and of the
+    // division); g_a from the ratio of fl32 h rounded up plus 4e-7 (the
+    // rounding of both h).  NaN (a slot never built) is kept.
+    const float dabs = 4.f * 5.9604645e-8f * sc->xmax_f;
+    float qm = 0.f;
     if (l < nleaves) {
         const int j0 = leaf_start[l], j1 = leaf_start[l + 1];
         float4 q[kLeaf];
@@ -566,8 +570,9 @@ __global__ void k_tree(const float4 *pos4, const float4 *pos_build, const int32_
         for (int k = 0; k < kLeaf; ++k) {
             const float4 qb = pos_build[j0 + k < j1 ? j0 + k : j0];
             const float dx = q[k].x - qb.x, dy = q[k].y - qb.y, dz = q[k].z - qb.z;
-            d2 = fmaxf(d2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            gr = fmaxf(gr, __fdiv_ru(q[k].w, qb.w) - 1.f);
+            const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * 1.000001f + dabs;
+            const float qa = __fdiv_ru(d, qb.w) * 1.000001f + (__fdiv_ru(q[k].w, qb.w) - 1.f) + 4e-7f;
+            qm = (qa > qm || qa != qa) ? qa : qm;
         }
         float lo[3] = {q[0].x, q[0].y, q[0].z}, hi[3] = {q[0].x, q[0].y, q[0].z}, hm = q[0].w;
 #pragma unroll
@@ -622,16 +627,13 @@ __global__ void k_tree(const float4 *pos4, const float4 *pos_build, const int32_
         }
         __syncthreads();
     }
-    // displacement and growth since the build: one atomic per warp
+    // largest q since the build: one atomic per warp on the bits of a
+    // non-negative float (or NaN, whose bits order above every number)
     for (int o = 16; o > 0; o >>= 1) {
-        d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-        gr = fmaxf(gr, __shfl_xor_sync(0xffffffffu, gr, o));
+        const float qo = __shfl_xor_sync(0xffffffffu, qm, o);
+        qm = (qo > qm || qo != qo) ? qo : qm;
     }
-    if ((t & 31) == 0) {
-        // NaN (lists never built) orders above every number: a rebuild
-        atomicMax(&sc->disp2_max, __float_as_uint(d2));
-        if (gr > 0.f || gr != gr) atomicMax(&sc->growth_max, __float_as_uint(gr));
-    }
+    if ((t & 31) == 0 && (qm > 0.f || qm != qm)) atomicMax(&sc->q_max, __float_as_uint(qm));
     __shared__ bool last;
     if (t == 0) {
         __threadfence();

@@ -84,9 +84,7 @@ struct DevScalars {
     // candidate-list reuse (all FP32 as bit patterns of non-negative floats
     // where noted, so atomicMax orders them)
     float skin;                      // eps of the candidate lists (< 0: rebuild every RHS)
-    float hmin_build;                // smallest h when the lists were built
-    unsigned int disp2_max;          // largest squared displacement since the build (float bits)
-    unsigned int growth_max;         // largest h/h_build - 1 (float bits)
+    unsigned int q_max;              // largest d_a / h_a0 + g_a since the build (float bits)
     int built;                       // candidate lists exist for the current order
     int resorted;                    // this RHS sorted along the curve again
     int rebuild;                     // this RHS rebuilds the candidate lists

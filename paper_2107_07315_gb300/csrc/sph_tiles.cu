@@ -415,7 +415,6 @@ k_tiles(DevState st, Scratch s, TreeLevels tl, int nleaves, int cap)
             s.vcnt[i] = min(cnt, cap);
             const float4 p = s_p[w][kLeaf * g + q];
             s.pos_build[i] = p;  // the positions and h these lists hold for
-            atomicMin((unsigned *)&sc->hmin_build, __float_as_uint(p.w));
         }
         __syncwarp();  // s_stage, s_lr, s_mask and s_sel are reused by the next leaf
     }

@@ -166,6 +166,31 @@ def test_checkpoint_resume_bit_exact(prec, sort_every):
         assert np.array_equal(res[k], full[k]), k
 
 
+@pytest.mark.parametrize("prec", [sph.SPH_FP64, sph.SPH_MIXED])
+def test_restore_into_the_same_context_after_a_sort(prec):
+    # steps 0-1, checkpoint, steps 2-5 (a sort at step 3 gives a new order and
+    # new candidate lists); restoring the checkpoint in the same context and
+    # stepping 2-5 again repeats the first pass bit for bit: the candidate
+    # lists of the later order are not reused for the restored one
+    opts = dict(sort_every=3)
+    st, eos = I.random_state(2500, seed=16, vel=0.2, stress=0.05)
+    dev = sph.device_state(st)
+    ctx = _ctx(dev, eos, MAT, None, prec, opts)
+    sph.sph_step(ctx, 1e-3, 2)
+    blob = sph.sph_get_state(ctx)
+    sph.sph_step(ctx, 1e-3, 4)
+    sph.sph_sync(ctx)
+    first = sph.to_numpy(dev)
+    builds = sph.sph_stats(ctx)[18]
+    sph.sph_set_state(ctx, blob)
+    sph.sph_step(ctx, 1e-3, 4)
+    sph.sph_sync(ctx)
+    again = sph.to_numpy(dev)
+    for k in KEYS + ("flags",):
+        assert np.array_equal(again[k], first[k]), k
+    assert sph.sph_stats(ctx)[18] > builds  # the restore forced a build
+
+
 @pytest.mark.parametrize("prec, rel", [(sph.SPH_FP64, 1e-12), (sph.SPH_MIXED, 2e-5)])
 def test_sort_every_keeps_lists_exact(prec, rel):
     # steps 1-3 of sort_every = 4 keep the order of step 0's sort: the lists
