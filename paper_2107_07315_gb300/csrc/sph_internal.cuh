@@ -34,6 +34,7 @@
 //                  the curve keys of a star are taken over its own box.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -94,6 +95,9 @@ struct DevScalars {
     unsigned int pq_head;            // next item to dequeue
     unsigned int pq_done;            // screening items completed
 };
+// the autotuner clears both queue counters with one 8-byte memset
+static_assert(offsetof(DevScalars, pq_done) == offsetof(DevScalars, pq_head) + sizeof(unsigned int),
+              "pq_head and pq_done must be adjacent");
 
 struct DevState {
     int64_t n;
