@@ -141,10 +141,11 @@ typedef struct {
  * must fit too); more raise SPH_ERR_CAPACITY at sph_sync.  The context
  * holds two int32 lists of this length per particle [0: 256].
  * lanes_per_particle: 4 or 8 threads share one particle's list in the pair
- * kernels [0: 8]; -1 turns on the autotuner of the lane counts: sph_init evaluates one
- * right-hand side on the bound state (writing the rates), then times the
- * exact screening with 4 and 8 threads per particle and the pair kernels
- * with 4 and 8, keeps the faster of each and restores the counters.  The
+ * kernels [0: 8]; -1 turns on the autotuner of the launch shape: sph_init
+ * evaluates one right-hand side on the bound state (writing the rates),
+ * then times the exact screening with 4 and 8 threads per particle, the
+ * pair kernels with 4 and 8 and the candidate build with search_leaves 1, 2
+ * and 4, keeps the fastest of each and restores the counters.  The
  * choice is cached for the process under (device, n, stars, precision,
  * max_neighbors, metric, any solid), so a later context of that
  * configuration reuses it without timing.  Lane counts set the order of the
@@ -155,7 +156,8 @@ typedef struct {
  * search_leaves: tree leaves (8 sorted particles each) that share one walk
  * of the candidate-list search, 1, 2 or 4; the candidate lists are the same
  * for each, only the cost of a build differs; a walk holds at most 256
- * candidate leaves for 1 and 512 for 2 or 4 [0: 1; with lanes_per_particle
+ * candidate leaves for 1 and 512 for 2 or 4 (1024 with one tree leaf per
+ * walk when max_neighbors is above 256) [0: 1; with lanes_per_particle
  * -1 the autotuner times all three and takes the fastest whose walk fills at
  * most half of its capacity on the bound state].
  * persistent: 1 runs the exact screening, density, equation of state and
@@ -171,17 +173,18 @@ typedef struct {
  * totals_every: compute totals every k steps inside sph_step [0: never].
  * sort_every: sph_step sorts the particles along the space-filling curve on
  * steps 0, k, 2k, ... (counted by the step counter) and keeps the last
- * sort's order on the others; every step still rebuilds the tree and the
- * neighbour lists from the current positions, so the lists are the same
- * sets (only the order of pair sums, hence rounding, depends on k)
- * [0 or 1: every step].  sph_rhs always sorts.
+ * sort's order on the others; every step still rebuilds the tree and
+ * screens the exact neighbour lists from the current positions, so the
+ * lists are the same sets (only the order of pair sums, hence rounding,
+ * depends on k) [0 or 1: every step].  sph_rhs always sorts.
  * skin: the neighbour search builds candidate lists of every pair within
  * (1 + skin)(h_a + h_b) and screens them exactly on every right-hand side;
- * it builds them again after a curve sort or once a particle may have moved
- * or grown into a pair they miss (a device-side test on the largest
- * displacement and h growth since the build), so the exact lists are the
- * same as with lists built every time [0: 0.1; negative: build on every
- * right-hand side; at most 1]. */
+ * it builds them again after a curve sort, after sph_set_state or
+ * sph_set_max_neighbors, or once a particle may have moved or grown into a
+ * pair they miss (a device-side test: the largest displacement over own h
+ * plus relative h growth of any particle since the build reaching skin),
+ * so the exact lists are the same as with lists built every time [0: 0.1;
+ * negative: build on every right-hand side; at most 1]. */
 typedef struct {
     int32_t h_nmin, h_nmax;
     int32_t max_neighbors;
