@@ -1124,8 +1124,9 @@ def main():
                     help="with --tune 0: 1 runs screening + force as one persistent launch")
     ap.add_argument("--mode-check", type=int, default=1,
                     help="also measure the mixed/FP64 speed-up at equal radial-mode accuracy")
-    ap.add_argument("--sort-every", type=int, default=8,
-                    help="curve sort every k steps (tree and lists are rebuilt every step)")
+    ap.add_argument("--sort-every", type=int, default=16,
+                    help="curve sort every k steps (tree and exact lists every step; candidate "
+                         "lists at the sorts and when stale)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
