@@ -254,7 +254,7 @@ sph_status sph_set_max_neighbors(sph_ctx *ctx, int32_t max_neighbors);
  * range before it is used for an access; one outside raises a device error
  * flag, the access goes to an index in range, and sph_sync reports
  * SPH_ERR_BOUNDS.  sph_build_checked returns 1 in such a build, 0 otherwise.
- * Library service (SURVEY's sanitizer substitute), no counterpart in the
+ * Library service (stands in for a memory sanitizer), no counterpart in the
  * paper. */
 int32_t sph_build_checked(void);
 
