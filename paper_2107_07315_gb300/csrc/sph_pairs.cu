@@ -433,7 +433,11 @@ k_rhs_persistent(int64_t n, DevState st, Scratch s, DevEos eos, DevMaterial mat,
     __shared__ float s_acc[A_N][PB];
     __shared__ int s_item, s_ok;
     DevScalars *sc = s.sc;
-    if (order_invalid(sc)) return;  // uniform: set before this launch
+    // one reading for the whole block: a force item of this launch may raise
+    // the timeout while the block starts
+    if (threadIdx.x == 0) s_ok = order_invalid(sc) ? 0 : 1;
+    __syncthreads();
+    if (!s_ok) return;
     const int total = n_screen + n_force;
     for (;;) {
         __syncthreads();  // the last item is done with s_acc and s_item
