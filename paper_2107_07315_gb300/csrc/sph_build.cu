@@ -352,9 +352,13 @@ __global__ void k_onesweep(const unsigned long long *kin, const uint32_t *vin,
     __shared__ uint32_t run[256];
     __shared__ uint32_t wsum[kSortThreads / 32];
     __shared__ uint32_t wc[kSortThreads / 32][256];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_abort;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (order_invalid(sc)) return;  // uniform: set by an earlier pass
+    // set by an earlier pass, or by a tile of this pass that gave up: one
+    // reading for the whole block, so that the block returns as one
+    if (t == 0) s_abort = order_invalid(sc) ? 1 : 0;
+    __syncthreads();
+    if (s_abort) return;
     const int limit = spin_limit_of(sc);
     if (t == 0) s_tile = (int)atomicAdd(tile_next, 1u);
     cnt[t] = 0u;
