@@ -673,7 +673,7 @@ def _series_run(st, eos, met, prec, dt, nsteps, every, dev, stream, options):
     r0 = np.sqrt(st["x"] ** 2 + st["y"] ** 2 + st["z"] ** 2)
     core = torch.from_numpy(r0 < 0.2 * r0.max()).to(dev)
     m = d["m"]
-    ms, t, rho, qzz = 0.0, [], [], []
+    ms, t, rho, qzz, eint = 0.0, [], [], [], []
     for k in range(0, nsteps + 1, every):
         if k:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -692,12 +692,13 @@ def _series_run(st, eos, met, prec, dt, nsteps, every, dev, stream, options):
         c = [float((m * d[a]).sum() / m.sum()) for a in ("x", "y", "z")]
         x, y, z = d["x"] - c[0], d["y"] - c[1], d["z"] - c[2]
         qzz.append(float((m * (z * z - (x * x + y * y + z * z) / 3.0)).sum()))
+        eint.append(float(sph.sph_totals(ctx)[5]))  # sum m u, the paper's radial-mode signal
     out = sph.to_numpy(d)
     stats = sph.sph_stats(ctx)
     sph.sph_free(ctx)
     del d, rates
     torch.cuda.empty_cache()
-    return np.array(t), np.array(rho), np.array(qzz), ms / nsteps, out, stats
+    return np.array(t), np.array(rho), np.array(qzz), ms / nsteps, out, stats, np.array(eint)
 
 
 def campaign(args):
@@ -729,16 +730,19 @@ def campaign(args):
         every = max(1, steps // 250)
         res, ser = {}, {}
         for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
-            t, rho, q, ms, _, stats = _series_run(st, eos, met, prec, dt, steps, every, dev, stream,
-                                                  opts)
-            ser[name] = (rho, q)
-            res[name] = {"omega_radial": _fit_omega(t, rho), "omega_quadrupole": _fit_omega(t, q),
+            t, rho, q, ms, _, stats, eu = _series_run(st, eos, met, prec, dt, steps, every, dev,
+                                                      stream, opts)
+            ser[name] = (rho, q, eu)
+            res[name] = {"omega_radial": _fit_omega(t, rho),
+                         "omega_radial_internal_energy": _fit_omega(t, eu),
+                         "omega_quadrupole": _fit_omega(t, q),
                          "ms_per_step": ms, "pairs_per_step": int(stats[0])}
         if args.campaign_out:
             np.savez(args.campaign_out, t=t, rho_mixed=ser["mixed"][0], qzz_mixed=ser["mixed"][1],
-                     rho_fp64=ser["fp64"][0], qzz_fp64=ser["fp64"][1])
+                     eint_mixed=ser["mixed"][2], rho_fp64=ser["fp64"][0], qzz_fp64=ser["fp64"][1],
+                     eint_fp64=ser["fp64"][2])
         # how closely the two runs' series agree, against each series' swing
-        for j, key in ((0, "core_density"), (1, "qzz")):
+        for j, key in ((0, "core_density"), (1, "qzz"), (2, "internal_energy")):
             a, b = ser["mixed"][j], ser["fp64"][j]
             out[key + "_max_diff_over_swing"] = float(np.max(np.abs(a - b)) / (np.ptp(b) or 1.0))
         out["radial_periods_covered"] = res["fp64"]["omega_radial"] * steps * dt / (2 * math.pi)
@@ -746,6 +750,9 @@ def campaign(args):
                     "mixed": res["mixed"], "fp64": res["fp64"],
                     "radial_rel_diff": abs(res["mixed"]["omega_radial"] /
                                            res["fp64"]["omega_radial"] - 1.0),
+                    "radial_internal_energy_rel_diff": abs(
+                        res["mixed"]["omega_radial_internal_energy"] /
+                        res["fp64"]["omega_radial_internal_energy"] - 1.0),
                     "quadrupole_rel_diff": abs(res["mixed"]["omega_quadrupole"] /
                                                res["fp64"]["omega_quadrupole"] - 1.0),
                     "speedup": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]})
